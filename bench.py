@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the ESC hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the selectivity sub-query workload over the resident
+skewed table: 60,000,000 rows x 8 columns (32 B/row; Zipf keys, correlated
+dictionary codes), 200 seeded predicates of 1-6 terms aimed at selectivities
+1e-6 .. 0.9, each returning its exact count and the ordered compaction of 3
+projected columns (key, day, price).  Every sub-query is one call of
+esc_selectivity_async through the C ABI.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ESC scan rows/s & HBM GB/s vs ~8 TB/s; p50/p99 per-sub-query latency"
+WORKLOAD = ("skewed table 60M rows x 8 cols (32 B/row), 200 predicates (1-6 terms, sel 1e-6..0.9), "
+            "exact count + ordered compaction of (key, day, price) per predicate")
+WIDTH = {"i32": 4, "i64": 8, "u8": 1, "u16": 2}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="esc", choices=["esc", "reference"])
+    ap.add_argument("--rows", type=int, default=60_000_000)
+    ap.add_argument("--preds", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for p in ("paper_1901_01488_gb300/csrc/esc_scan.cu", "paper_1901_01488_gb300/csrc/esc_internal.h"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "scan_kernel.skewed_60m_200preds.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_digest") != source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pred_refs(pred) -> list:
+    """Columns a compiled predicate reads, from the library's program listing."""
+    refs = []
+    for line in pred.explain().splitlines():
+        f = line.split()
+        if f and f[0] == "ref":
+            refs.append((f[2], f[3]))
+    return refs
+
+
+def algorithmic_bytes(nrows, refs, proj_types, count):
+    ref_names = {n for n, _ in refs}
+    read = nrows * sum(WIDTH[t] for _, t in refs)
+    gather = count * sum(WIDTH[t] for n, t in proj_types if n not in ref_names)
+    write = count * (4 + sum(WIDTH[t] for _, t in proj_types))
+    return read + gather + write
+
+
+def cpu_baseline(host_cols, preds, proj, budget_s):
+    """The oracle as it stands (single-threaded C tree walker + numpy gather)."""
+    import oracle
+    nrows_avail = len(next(iter(host_cols.values())))
+    sample = min(nrows_avail, 1_000_000)
+    cols = {k: v[:sample] for k, v in host_cols.items()}
+    done_rows, t0, used = 0, time.perf_counter(), 0
+    for p in preds:
+        oracle.select(p.text, cols, proj)
+        done_rows += sample
+        used += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done_rows / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample:,} rows of the 60M-row table x {used} of {len(preds)} predicates "
+                      f"(count + ordered ids + projection), {dt:.1f} s, single-threaded C"}
+
+
+# ---------------------------------------------------------------------------- ESC arm
+def run_esc(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1901_01488_gb300 import build as esc_build
+    esc_build.build()
+    from paper_1901_01488_gb300 import datagen, esc
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t = datagen.skewed_table(args.rows, seed=2 + rank, device=dev)
+    table = esc.Table.from_datagen(t)
+    ptexts = datagen.skewed_predicates(args.preds)
+    proj = datagen.SKEWED_PROJECTION
+    preds = [esc.Predicate(table, p.text, proj) for p in ptexts]
+    proj_types = [(n, table.dtype(n)) for n in proj]
+    counts = [esc.count(table, p) for p in preds]
+    cap = max(1, max(counts))
+    rows = preds[0].alloc_rows(cap, device=dev)
+    refs = [pred_refs(p) for p in preds]
+    alg = [algorithmic_bytes(args.rows, r, proj_types, c) for r, c in zip(refs, counts)]
+    dev_counts = torch.zeros(len(preds), dtype=torch.int64, device=dev)
+    K, W = args.steps, args.warmup
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in preds]
+          for _ in range(K)]
+
+    def step(k=None):
+        for j, p in enumerate(preds):
+            if k is not None:
+                ev[k][j][0].record(stream)
+            esc.esc_selectivity_async(table.handle, p.handle, dev_counts[j:j + 1], rows, stream)
+            if k is not None:
+                ev[k][j][1].record(stream)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        t_start.record(stream)
+        for k in range(K):
+            step(k)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = t_start.elapsed_time(t_end)
+    if dist:
+        x = torch.tensor([ms], device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    assert dev_counts.tolist() == counts, "counts changed between runs"
+    per_q = [[ev[k][j][0].elapsed_time(ev[k][j][1]) for j in range(len(preds))] for k in range(K)]
+    lat = sorted(x for row in per_q for x in row)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    kern_s = sum(sum(row) for row in per_q) / 1e3
+    achieved = sum(alg) * K / kern_s / 1e9
+    peak, peak_src = measured_peak_hbm()
+    rows_total = args.rows * len(preds) * K * world
+    value = rows_total / (ms / 1e3)
+    step_gbs = sum(alg) * K * world / (ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of the columns, the
+    # 200 sub-queries, D2H of the counts, every step
+    host = [c.data.cpu().pin_memory() for c in t.columns]
+    host_counts = torch.zeros(len(preds), dtype=torch.int64).pin_memory()
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for _ in range(args.e2e_steps):
+        for c, h in zip(t.columns, host):
+            c.data.copy_(h, non_blocking=True)
+        step()
+        host_counts.copy_(dev_counts, non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e_start.elapsed_time(e_end) / args.e2e_steps
+    assert host_counts.tolist() == counts
+    e2e_value = args.rows * len(preds) * world / (e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        hc = {c.name: datagen.Column(c.name, c.dtype, c.data[:1_000_000]).numpy() for c in t.columns}
+        cpu = cpu_baseline(hc, ptexts, proj, args.cpu_seconds)
+
+    if rank == 0:
+        sel = sorted(c / args.rows for c in counts)
+        out = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": args.rows, "predicates": len(preds),
+                       "projection": list(proj), "bytes_per_row": t.row_bytes,
+                       "l2": "inputs larger than L2 (1.92 GB table per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "selectivity_min_median_max": [sel[0], sel[len(sel) // 2], sel[-1]]},
+            "hbm_gbs_algorithmic": step_gbs,
+            "latency_ms": {"p50": p50, "p99": p99, "what": "device time of one sub-query call (events on its stream)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(),
+                         "kernel": "esc::scan_kernel", "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": sum(alg) / len(alg)},
+            "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": host_counts.numel() * 8},
+            "gpu_launches": K * len(preds),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import torch
+    import oracle
+    from paper_1901_01488_gb300 import datagen
+    K, W = args.steps, args.warmup
+    ptexts = datagen.skewed_predicates(args.preds)
+    proj = datagen.SKEWED_PROJECTION
+    # bounded sample: a row window per step, sized so the whole run takes ~ --cpu-seconds x 4
+    per_row_pred_s = 110e-9
+    window = int(max(2_000, min(1_000_000, args.cpu_seconds * 4 / (K + W) / (len(ptexts) * per_row_pred_s))))
+    total = window * (K + W)
+    t = datagen.skewed_table(total, seed=2, device="cpu")
+    host = t.host()
+    times = []
+    for s in range(K + W):
+        cols = {k: v[s * window:(s + 1) * window] for k, v in host.items()}
+        t0 = time.perf_counter()
+        for p in ptexts:
+            oracle.select(p.text, cols, proj)
+        if s >= W:
+            times.append(time.perf_counter() - t0)
+    sec = sum(times)
+    value = window * len(ptexts) * K / sec
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": sec / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": args.rows, "predicates": len(ptexts), "projection": list(proj),
+                   "l2": "n/a (CPU)", "sample_rows_per_step": window},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{window:,}-row window of the same generator per step x {len(ptexts)} predicates, "
+                                   f"single-threaded C tree walker + numpy gather"},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_esc(args)
+
+
+if __name__ == "__main__":
+    main()

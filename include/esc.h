@@ -1,0 +1,212 @@
+/*
+ * esc.h -- C ABI of the GB300 exact selectivity computation library (libesc).
+ *
+ * Exact selectivity computation (ESC; Shin, Rusu, Suhan, "Exact Selectivity
+ * Computation for Modern In-Memory Database Query Optimization", CIDR 2019)
+ * replaces a cardinality estimate by the answer of a selectivity sub-query
+ * run during optimisation (Sec. 2): the number of rows of one table that
+ * satisfy a complex selection predicate, and optionally those rows with a
+ * pushed-down projection, materialised for reuse by the final plan
+ * (Sec. 2, Sec. 2.1).  This library runs that sub-query on one GPU over
+ * resident columns, and adds exact filtered-join counts over dense keys
+ * (the COUNT(*) foreign-key join queries of Sec. 3.1) and batched execution
+ * of many sub-queries (Sec. 2: the procedure is applied to every table that
+ * has a selection).
+ *
+ * Conventions for every entry point
+ *  - Every call returns an esc_status; ESC_OK is 0.  On any other status the
+ *    outputs are undefined, except where a function says otherwise, and
+ *    esc_last_error() returns a message for the calling thread.
+ *  - Device pointers are CUDA device (or managed) addresses on the current
+ *    device; host pointers are ordinary process memory.  The library never
+ *    takes ownership of caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; functions that return host values
+ *    synchronise that stream before returning, *_async functions do not.
+ *  - Calls are thread-safe for distinct handles.  Handles are immutable after
+ *    creation and may be shared by concurrent calls on different streams.
+ *  - Device-side errors (a bounded wait that gave up) come back as
+ *    ESC_ETIMEOUT from synchronous calls; no kernel traps or asserts.
+ */
+#ifndef ESC_H
+#define ESC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum esc_status {
+    ESC_OK = 0,
+    ESC_EINVAL = 1,    /* bad argument, size, alignment, or predicate text */
+    ESC_ETYPE = 2,     /* unsupported column type or a type mismatch */
+    ESC_ENOMEM = 3,    /* device or host allocation failed */
+    ESC_ETRUNC = 4,    /* output rows did not fit: count is exact, rows truncated */
+    ESC_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    ESC_EBUSY = 6,     /* resource in use */
+    ESC_ECUDA = 7      /* a CUDA runtime call failed */
+} esc_status;
+
+/* Column element types.  Values are widened to int64 for every comparison:
+ * signed types sign-extend, unsigned types zero-extend. */
+typedef enum esc_dtype { ESC_I32 = 0, ESC_I64 = 1, ESC_U8 = 2, ESC_U16 = 3 } esc_dtype;
+
+/* One column of a table: `data` is a device array of nrows elements of
+ * `dtype`, 16-byte aligned.  `name` is copied at table creation. */
+typedef struct esc_column {
+    const char *name;
+    int32_t dtype;        /* esc_dtype */
+    const void *data;     /* device pointer, borrowed */
+} esc_column;
+
+typedef struct esc_table esc_table;   /* opaque column-store table */
+typedef struct esc_pred esc_pred;     /* opaque compiled predicate bound to a table */
+typedef struct esc_batch esc_batch;   /* opaque prepared batch of sub-queries */
+
+/* Caller-owned output buffers for the materialised sub-query result.
+ * row_ids: device array of `capacity` uint32 row ids, written in ascending
+ * order.  proj: host array of nproj device pointers, one per projected
+ * column (in the order given to esc_predicate_compile), each an array of
+ * `capacity` elements of that column's type.  `written` is set by
+ * synchronous calls to min(count, capacity). */
+typedef struct esc_rows {
+    uint64_t capacity;
+    uint32_t *row_ids;
+    void *const *proj;
+    uint64_t written;
+} esc_rows;
+
+/* ---------------------------------------------------------------- tables */
+
+/* Columnar table store (Sec. 2: column-wise in-memory tables).  Registers
+ * `ncols` (1..64) borrowed device columns of `nrows` rows each (nrows < 2^32;
+ * 0 is allowed).  Column names must be distinct identifiers.  Each `data`
+ * must be 16-byte aligned (ESC_EINVAL otherwise) and stay valid until
+ * esc_table_destroy.  Unknown dtypes give ESC_ETYPE.  *out is owned by the
+ * caller and released with esc_table_destroy. */
+esc_status esc_table_create(const esc_column *cols, int32_t ncols, uint64_t nrows,
+                            esc_table **out);
+esc_status esc_table_destroy(esc_table *table);
+uint64_t esc_table_nrows(const esc_table *table);
+
+/* ---------------------------------------------------------------- predicates */
+
+/* Compiles a selection predicate (the WHERE clause of the selectivity
+ * sub-query, Sec. 1 and Sec. 2) over `table` into a flat postfix program,
+ * and binds the projection pushed down with it (Sec. 2: the columns later
+ * operators need).
+ *
+ * Language (keywords case-insensitive, column names case-sensitive):
+ *   pred    := or;  or := and (OR and)*;  and := unary (AND unary)*
+ *   unary   := NOT unary | '(' pred ')' | TRUE | FALSE | test
+ *   test    := operand cmp INT | operand [NOT] BETWEEN INT AND INT
+ *            | operand [NOT] IN '(' [INT (',' INT)*] ')'
+ *   operand := column | udf '(' column ',' column ',' INT ')'
+ *   cmp     := = | == | != | <> | < | <= | > | >=
+ * INT is a decimal int64.  BETWEEN is inclusive (empty when lo > hi).
+ * udf(a, b, m) is (a * b) mod m with the product wrapping in 64-bit two's
+ * complement and the remainder truncated toward zero; m must be > 0.
+ * An IN list holds at most 16 values; an empty list is false.
+ *
+ * proj: `nproj` (0..16) column names to materialise.  Limits: at most 16
+ * distinct columns read by the predicate, 64 program instructions, nesting
+ * that needs at most 8 evaluation-stack entries; each violation, a syntax
+ * error, an unknown column or m <= 0 gives ESC_EINVAL with a message.
+ * *out is released with esc_predicate_destroy; the table must outlive it. */
+esc_status esc_predicate_compile(const esc_table *table, const char *text,
+                                 const char *const *proj, int32_t nproj, esc_pred **out);
+esc_status esc_predicate_destroy(esc_pred *pred);
+
+/* Writes a NUL-terminated listing of the compiled program (read columns,
+ * projection, one line per instruction) into buf[0..buflen).  ESC_EINVAL if
+ * it does not fit. */
+esc_status esc_predicate_explain(const esc_pred *pred, char *buf, uint64_t buflen);
+
+/* ---------------------------------------------------------------- sub-queries */
+
+/* The selectivity sub-query (Sec. 2): *count (host) receives the exact
+ * number of rows of `table` satisfying `pred`.  When `rows` is not NULL the
+ * qualifying rows are also materialised (Sec. 2.1): their ids in ascending
+ * order and their projected columns, in the caller's buffers.  If count >
+ * rows->capacity, the first `capacity` rows are written, rows->written =
+ * capacity, *count is still exact and the status is ESC_ETRUNC.
+ * Synchronises `stream`.  `pred` must have been compiled against `table`. */
+esc_status esc_selectivity(const esc_table *table, const esc_pred *pred, uint64_t *count,
+                           esc_rows *rows, void *stream);
+
+/* Same as esc_selectivity without synchronising: the exact count is written
+ * to the device word *dev_count when the stream reaches that point, and
+ * rows->written is not set (it is min(count, capacity)).  Truncation and
+ * device-side timeouts are not reported by this call. */
+esc_status esc_selectivity_async(const esc_table *table, const esc_pred *pred,
+                                 uint64_t *dev_count, esc_rows *rows, void *stream);
+
+/* Batched sub-queries (Sec. 2: one per table that has a selection): the n
+ * pairs (tables[i], preds[i]) run in one persistent kernel launch, captured
+ * in a CUDA graph at prepare time.  rows may be NULL (counts only) or an
+ * array of n esc_rows whose entries with capacity 0 and row_ids NULL are
+ * count-only.  All buffers are borrowed and must stay valid until
+ * esc_batch_destroy.  esc_batch_run writes n exact counts to the device
+ * array dev_counts and, if dev_done_ns is not NULL, the device time
+ * (%globaltimer, ns) at which each sub-query's last tile finished.  Runs
+ * enqueued on one stream are ordered; concurrent runs of the same batch on
+ * different streams are not allowed (ESC_EBUSY is not detected). */
+esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *const *preds,
+                             int32_t n, const esc_rows *rows, esc_batch **out);
+esc_status esc_batch_run(esc_batch *batch, uint64_t *dev_counts, uint64_t *dev_done_ns,
+                         void *stream);
+esc_status esc_batch_destroy(esc_batch *batch);
+
+/* One-shot form of the above: prepares, runs, synchronises and destroys.
+ * counts is a host array of n entries. */
+esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred *const *preds,
+                                 int32_t n, uint64_t *counts, esc_rows *rows, void *stream);
+
+/* ---------------------------------------------------------------- joins */
+
+/* Dense-key bitmap of a filtered dimension table: bit k of the device array
+ * dev_bitmap (word k / 32, bit k % 32, little-endian bit order) is set when
+ * row k -- the row whose dense key is k -- satisfies pred.  dev_bitmap holds
+ * ceil(nrows / 32) uint32 words, all of which are written.  *count (host,
+ * may be NULL) receives the number of set bits.  Synchronises `stream`. */
+esc_status esc_bitmap_build(const esc_table *dim, const esc_pred *pred, uint32_t *dev_bitmap,
+                            uint64_t *count, void *stream);
+
+/* Exact semi-join cardinalities of a fact table against filtered dimensions
+ * on dense keys (the COUNT(*) foreign-key join queries of Sec. 3.1):
+ * for every subset S of the ndims (1..4) dimensions, subset_counts[S] (host,
+ * 2^ndims entries, bit d of S = dimension d) receives
+ *   |{ i : for all d in S, 0 <= fk_d[i] < dim_rows[d] and bit fk_d[i] of
+ *          dev_bitmaps[d] is set }|,
+ * which equals |fact JOIN_S sigma(dims)| when dimension keys are dense and
+ * unique.  fk_cols names ndims distinct ESC_I32 columns of `fact`.
+ * dev_bitmaps[d] (host array of device pointers) holds ceil(dim_rows[d]/32)
+ * words.  Synchronises `stream`. */
+esc_status esc_semijoin_counts(const esc_table *fact, const char *const *fk_cols, int32_t ndims,
+                               const uint32_t *const *dev_bitmaps, const uint64_t *dim_rows,
+                               uint64_t *subset_counts, void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message for the last non-OK status returned to the calling thread. */
+const char *esc_last_error(void);
+const char *esc_status_string(esc_status status);
+
+/* Multiplier and shifts used to divide by the udf modulus d (d >= 1) with a
+ * multiply-high, after Granlund and Montgomery, "Division by Invariant
+ * Integers using Multiplication" (PLDI 1994), Fig. 4.1: for every 64-bit n,
+ * t = mulhi(mult, n), n / d = (t + ((n - t) >> sh1)) >> sh2. */
+esc_status esc_udf_magic(uint64_t d, uint64_t *mult, int32_t *sh1, int32_t *sh2);
+
+/* Runs a one-CTA kernel that waits on a device flag nothing sets, with the
+ * same bounded wait the scan kernels use, giving up after about `limit_ns`
+ * nanoseconds.  Returns ESC_ETIMEOUT when the wait gave up (the expected
+ * outcome) and leaves the context usable.  Exercises failure detection
+ * without faulting a GPU. */
+esc_status esc_selftest_wait_timeout(uint64_t limit_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESC_H */

@@ -1,0 +1,132 @@
+// Internal layout shared by the host compiler (esc_host.cpp) and the CUDA
+// kernels (esc_scan.cu, esc_semijoin.cu).  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/esc.h"
+
+#ifdef __CUDACC__
+#define ESC_HD __host__ __device__
+#else
+#define ESC_HD
+#endif
+
+namespace esc {
+
+constexpr int kMaxInstr = 64;   // program length
+constexpr int kMaxRef = 16;     // distinct columns a predicate reads
+constexpr int kMaxProj = 16;    // projected columns
+constexpr int kMaxPool = 128;   // int64 constants (IN lists, udf divisors)
+constexpr int kMaxIn = 16;      // values in one IN list
+constexpr int kMaxDepth = 8;    // evaluation stack: 8 masks of 8 bits in one u64
+constexpr int kV = 8;           // rows per lane per group
+constexpr int kGroup = 256;     // rows per warp group (32 lanes x 8 rows)
+constexpr int kMaxTileRows = 32768;
+
+// Lane l of a warp owns, in a 256-row group, the rows
+//   64*j + 2*l + i   for j in 0..3, i in 0..1;
+// its 8-bit mask has bit 2*j + i for that row.  Each of the 4 loads per
+// column then reads 2 consecutive elements per lane, i.e. 32 lanes read one
+// contiguous run of 64 elements: conflict-free shared-memory access for
+// every element width.
+
+enum Op : uint8_t {
+  OP_RANGE = 0,   // push  lo <= col <= hi
+  OP_IN = 1,      // push  col in pool[off .. off+n)
+  OP_UDF = 2,     // push  lo <= (col*col2) mod m <= hi   (m, magic at pool[off..off+4))
+  OP_AND = 3,     // pop b, pop a, push a & b
+  OP_OR = 4,      // pop b, pop a, push a | b
+  OP_NOT = 5,     // top = ~top
+  OP_TRUE = 6,    // push all-ones
+  OP_FALSE = 7,   // push zero
+};
+
+struct Instr {
+  uint8_t op;
+  uint8_t dtype;    // esc_dtype of the (first) operand column
+  uint8_t dtype2;   // udf: esc_dtype of the second operand column
+  uint8_t ref;      // stage slot of the (first) operand column
+  uint8_t ref2;     // udf: stage slot of the second operand column
+  uint8_t pad0;
+  uint16_t n;       // IN: number of values
+  uint16_t off;     // IN / UDF: first pool entry
+  uint16_t pad1;
+  uint32_t pad2;
+  int64_t lo;       // inclusive range, already clamped to the operand's domain
+  int64_t hi;
+};
+static_assert(sizeof(Instr) == 32, "Instr layout");
+
+enum Mode : int32_t { MODE_COUNT = 0, MODE_COMPACT = 1, MODE_BITMAP = 2 };
+
+// One sub-query as the scan kernel sees it.  Built on the host per call (or
+// per prepared batch); read-only on the device.
+struct Query {
+  int32_t ninstr;
+  int32_t nref;
+  int32_t nproj;
+  int32_t mode;
+  uint32_t nrows;
+  uint32_t tile_rows;     // multiple of the CTA's rows per sweep
+  uint32_t ntiles;
+  uint32_t tile_base;     // first global ticket of this query
+  uint32_t stage_off[kMaxRef];    // byte offset of each read column in a stage
+  uint8_t ref_w[kMaxRef];         // element width of each read column
+  uint8_t proj_w[kMaxProj];
+  int8_t proj_ref[kMaxProj];      // stage slot holding the projected column, or -1
+  uint8_t pad[16];
+  const uint8_t *ref_ptr[kMaxRef];
+  const uint8_t *proj_ptr[kMaxProj];
+  void *out_proj[kMaxProj];
+  uint32_t *out_ids;
+  uint32_t *bitmap;
+  uint64_t capacity;
+  unsigned long long *count;      // exact count accumulates here (zeroed before launch)
+  unsigned long long *tile_status;// decoupled look-back words, ntiles (zeroed)
+  unsigned int *tiles_left;       // tiles not yet finished (set to ntiles before launch)
+  unsigned long long *done_ns;    // %globaltimer when the last tile finished (may be null)
+  Instr code[kMaxInstr];
+  int64_t pool[kMaxPool];
+};
+
+// Per-launch header in device scratch memory (zeroed before launch).
+struct ScratchHdr {
+  unsigned int ticket;   // next global tile ticket
+  unsigned int status;   // esc_status raised on the device (0 = OK)
+  unsigned int abort;    // set together with status; everyone stops working
+  unsigned int pad;
+};
+
+}  // namespace esc
+
+// ------------------------------------------------------------------ host side
+struct esc_table {
+  uint64_t nrows;
+  std::vector<std::string> names;
+  std::vector<int32_t> dtypes;
+  std::vector<const void *> data;
+};
+
+struct esc_pred {
+  const esc_table *table;
+  std::string text;
+  int32_t ninstr = 0;
+  std::vector<int32_t> ref_cols;    // table column index of each stage slot
+  std::vector<int32_t> proj_cols;   // table column index of each projected column
+  std::vector<int32_t> proj_ref;    // stage slot of each projected column or -1
+  std::vector<esc::Instr> code;
+  std::vector<int64_t> pool;
+  int32_t depth = 0;
+};
+
+namespace esc {
+int dtype_width(int32_t dt);
+esc_status fail(esc_status s, const std::string &msg);
+void clear_error();
+// Fills the static part of a Query (program, read columns, projection) for a pred.
+void fill_query_program(const esc_pred *p, Query *q);
+// Granlund-Montgomery unsigned magic for divisor d (Fig. 4.1 of their paper).
+void udiv_magic(uint64_t d, uint64_t *mult, int32_t *sh1, int32_t *sh2);
+}  // namespace esc

@@ -1,0 +1,161 @@
+"""Host-side checks of libesc (no GPU): exports, compiler errors, the compiled
+program's meaning (interpreted here with numpy, checked against the oracle),
+and the udf divisor constants.  No kernel is launched."""
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _helpers import host_table, as_columns, random_preds
+from paper_1901_01488_gb300 import build as esc_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def esc():
+    esc_build.build()
+    from paper_1901_01488_gb300 import esc as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(esc):
+    with open(os.path.join(ROOT, "include", "esc.h")) as f:
+        hdr = f.read()
+    declared = set(re.findall(r"^\s*(?:esc_status|const char \*|uint64_t)\s*(esc_\w+)\s*\(", hdr, re.M))
+    assert {"esc_table_create", "esc_predicate_compile", "esc_selectivity", "esc_selectivity_batch",
+            "esc_semijoin_counts", "esc_bitmap_build"} <= declared
+    for name in declared:
+        assert hasattr(esc._lib, name), name
+    assert declared <= set(esc.EXPORTED)
+
+
+def _table(esc, cols):
+    return esc.Table(as_columns(cols), len(next(iter(cols.values()))))
+
+
+def _interpret(listing: str, cols):
+    """Evaluates an EXPLAIN listing with numpy (this test's own interpreter)."""
+    refs = {}
+    stack = []
+    n = None
+    for line in listing.splitlines():
+        f = line.split()
+        if f[0] == "rows":
+            n = int(f[1])
+        elif f[0] == "ref":
+            refs[int(f[1])] = cols[f[2]].astype(np.int64)
+        elif f[0] == "instr":
+            op = f[2]
+            if op == "RANGE":
+                x = refs[int(f[3])]
+                stack.append((x >= int(f[5])) & (x <= int(f[6])))
+            elif op == "IN":
+                x = refs[int(f[3])]
+                stack.append(np.isin(x, [int(v) for v in f[5].split(",")]))
+            elif op == "UDF":
+                a, b = refs[int(f[3])], refs[int(f[5])]
+                with np.errstate(over="ignore"):
+                    p = a * b
+                r = np.fmod(p, int(f[7]))
+                stack.append((r >= int(f[8])) & (r <= int(f[9])))
+            elif op == "AND":
+                y = stack.pop(); stack.append(stack.pop() & y)
+            elif op == "OR":
+                y = stack.pop(); stack.append(stack.pop() | y)
+            elif op == "NOT":
+                stack.append(~stack.pop())
+            elif op == "TRUE":
+                stack.append(np.ones(n, dtype=bool))
+            elif op == "FALSE":
+                stack.append(np.zeros(n, dtype=bool))
+    assert len(stack) == 1
+    return stack[0]
+
+
+def test_compiled_program_means_the_predicate(esc):
+    cols = host_table()
+    t = _table(esc, cols)
+    checked = 0
+    for text in random_preds():
+        try:
+            p = esc.Predicate(t, text)
+        except esc.EscError as e:
+            assert "nests too deeply" in str(e) or "64 instructions" in str(e) or "pool" in str(e), (text, e)
+            continue
+        got = _interpret(p.explain(), cols)
+        ids, _ = oracle.select(text, cols)
+        assert np.array_equal(np.flatnonzero(got), ids.astype(np.int64)), text
+        checked += 1
+    assert checked > 300
+
+
+def test_compile_errors(esc):
+    cols = host_table(100)
+    t = _table(esc, cols)
+    bad = ["", "a =", "a BETWEEN 1", "a IN (1,", "udf(a, b, 0) > 1", "udf(a, b, -3) > 1",
+           "zz = 1", "a = 1 AND", "a NOT = 1", "a = 99999999999999999999", "(a = 1", "a = 1)",
+           "a ? 1", "a IN (" + ",".join(["1"] * 17) + ")"]
+    for text in bad:
+        with pytest.raises(esc.EscError) as ei:
+            esc.Predicate(t, text)
+        assert ei.value.status == esc.ESC_EINVAL, text
+    with pytest.raises(esc.EscError):
+        esc.Predicate(t, "a = 1", proj=("nope",))
+    deep = "a = 1"
+    for _ in range(10):
+        deep = f"(b = 2 OR ({deep} AND c = 3))"
+    p = esc.Predicate(t, deep)                      # Sethi-Ullman order keeps the stack shallow
+    depth = int(p.explain().split("depth ")[1].split()[0])
+    assert depth <= 3
+    long = " AND ".join(f"a != {k}" for k in range(40))   # 40 tests + 39 ANDs > 64 instructions
+    with pytest.raises(esc.EscError) as ei:
+        esc.Predicate(t, long)
+    assert "64 instructions" in str(ei.value)
+
+
+def test_constant_folding_and_domains(esc):
+    t = _table(esc, host_table(100))
+    assert "FALSE" in esc.Predicate(t, "b > 255").explain()
+    assert "TRUE" in esc.Predicate(t, "b >= 0").explain()
+    assert "FALSE" in esc.Predicate(t, "d BETWEEN 70000 AND 80000").explain()
+    assert "RANGE 0 i32 -2147483648 5" in esc.Predicate(t, "e <= 5").explain()
+    assert "FALSE" in esc.Predicate(t, "a IN ()").explain()
+    lst = esc.Predicate(t, "b IN (300, -1, 4, 4)").explain()
+    assert "RANGE 0 u8 4 4" in lst
+    assert "TRUE" in esc.Predicate(t, "NOT (b < 0)").explain()
+
+
+def test_table_create_errors(esc):
+    x = torch.zeros(64, dtype=torch.int32)
+    with pytest.raises(esc.EscError):
+        esc.esc_table_create([("a", "i32", x), ("a", "i32", x)], 64)
+    with pytest.raises(esc.EscError) as ei:
+        esc.esc_table_create([("a", "f32", x)], 64)
+    assert ei.value.status == esc.ESC_ETYPE
+    with pytest.raises(esc.EscError):
+        esc.esc_table_create([("a", "i32", x[1:])], 63)       # not 16-byte aligned
+    with pytest.raises(esc.EscError):
+        esc.esc_table_create([("1a", "i32", x)], 64)
+    with pytest.raises(esc.EscError):
+        esc.esc_table_create([("a", "i32", x)], 1 << 32)
+    h = esc.esc_table_create([("a", "i32", x)], 0)
+    esc.esc_table_destroy(h)
+
+
+def test_udf_magic_divides_exactly(esc):
+    rng = np.random.default_rng(1)
+    ds = [1, 2, 3, 7, 97, 1000, 1 << 20, (1 << 32) + 15, (1 << 62) + 1, (1 << 63) - 1, (1 << 63) + 5,
+          (1 << 64) - 1] + [int(x) for x in rng.integers(1, 1 << 62, 40)]
+    ns = [0, 1, (1 << 64) - 1, (1 << 63), (1 << 63) - 1] + [int(x) for x in rng.integers(0, 1 << 63, 200)]
+    ns += [int(x) * 2 + 1 for x in rng.integers(0, 1 << 62, 50)]
+    for d in ds:
+        mult, s1, s2 = esc.esc_udf_magic(d)
+        for n in ns + [d - 1, d, d + 1, 2 * d - 1, 2 * d]:
+            n &= (1 << 64) - 1
+            t = (mult * n) >> 64
+            q = (t + ((n - t) >> s1)) >> s2
+            assert q == n // d, (d, n)
