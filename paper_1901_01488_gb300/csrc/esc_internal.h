@@ -52,8 +52,9 @@ struct Instr {
   uint8_t pad0;
   uint16_t n;       // IN: number of values
   uint16_t off;     // IN / UDF: first pool entry
+  uint16_t soff;    // byte offset of the operand column's slice in a stage (set at launch)
+  uint16_t soff2;   // same for the udf's second column
   uint16_t pad1;
-  uint32_t pad2;
   int64_t lo;       // inclusive range, already clamped to the operand's domain
   int64_t hi;
 };
@@ -69,14 +70,18 @@ struct Query {
   int32_t nproj;
   int32_t mode;
   uint32_t nrows;
-  uint32_t tile_rows;     // multiple of the CTA's rows per sweep
+  uint32_t tile_rows;     // rows staged per tile, a multiple of kGroup
   uint32_t ntiles;
-  uint32_t tile_base;     // first global ticket of this query
+  uint32_t unit_tiles;    // tiles per work unit (one ticket, one look-back)
+  uint32_t nunits;
+  uint32_t unit_base;     // first global ticket of this query
+  uint32_t gmax;          // groups per full tile (tile_rows / kGroup)
+  uint32_t pad0;
   uint32_t stage_off[kMaxRef];    // byte offset of each read column in a stage
   uint8_t ref_w[kMaxRef];         // element width of each read column
   uint8_t proj_w[kMaxProj];
-  int8_t proj_ref[kMaxProj];      // stage slot holding the projected column, or -1
-  uint8_t pad[16];
+  int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
+  uint8_t pad[8];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];
@@ -84,12 +89,15 @@ struct Query {
   uint32_t *bitmap;
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
-  unsigned long long *tile_status;// decoupled look-back words, ntiles (zeroed)
-  unsigned int *tiles_left;       // tiles not yet finished (set to ntiles before launch)
+  unsigned long long *unit_status;// decoupled look-back words, one per unit (zeroed)
+  uint8_t *masks;                 // compaction scratch: 32 bytes per group (ntiles x gmax groups)
+  uint32_t *gcounts;              // compaction scratch: qualifying rows per group
+  unsigned int *tiles_left;       // consumer-warp tile visits left (ntiles x warps, set before launch)
   unsigned long long *done_ns;    // %globaltimer when the last tile finished (may be null)
   Instr code[kMaxInstr];
   int64_t pool[kMaxPool];
 };
+static_assert(sizeof(Query) % 16 == 0, "Query is copied with 16-byte vectors");
 
 // Per-launch header in device scratch memory (zeroed before launch).
 struct ScratchHdr {

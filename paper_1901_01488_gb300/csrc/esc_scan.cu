@@ -36,13 +36,13 @@
 
 namespace esc {
 
-constexpr int kConsumers = 8;                    // consumer warps per CTA
-constexpr int kThreads = 32 * (kConsumers + 1);  // + 1 producer warp
-constexpr int kStages = 3;
-constexpr uint32_t kStageBytes = 64 * 1024;
-constexpr int kMaxGroups = kMaxTileRows / kGroup;  // 128
+constexpr int kConsumers = 16;                   // consumer warps per CTA
+constexpr int kThreads = 32 * (kConsumers + 2);  // + producer warp + look-back warp
+constexpr int kStages = 4;
+constexpr uint32_t kStageBytes = 48 * 1024;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr uint32_t FULL = 0xffffffffu;
+static_assert(kStageBytes <= 65536, "stage offsets are 16-bit");
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -93,9 +93,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumers) : "memory");
-}
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -110,17 +107,41 @@ __device__ __forceinline__ bool aborted(const ScratchHdr *hdr) {
   return *(volatile const unsigned *)&hdr->abort != 0u;
 }
 
-// Bounded wait for the phase of parity `parity` of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, ScratchHdr *hdr) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Warp-collective bounded wait for the phase of parity `parity` of an
+// mbarrier: every lane must observe the completion itself (so that every lane
+// has acquire ordering), the warp leaves together, and the decision to give
+// up is lane 0's, broadcast.  With `abortable` the wait also gives up as
+// soon as the launch is aborting (used for every wait that does not guard an
+// in-flight bulk copy, so that one timeout cannot cascade into more).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, ScratchHdr *hdr,
+                                          uint64_t limit_ns = kWaitLimitNs, bool abortable = false) {
+  bool seen = mbar_try_wait(bar, parity);
+  if (__all_sync(FULL, seen)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) {
-      raise_status(hdr, ESC_ETIMEOUT);
-      return false;
+    if (!seen) seen = mbar_try_wait(bar, parity);
+    if (__all_sync(FULL, seen)) return true;
+    if ((it & 63u) == 0) {
+      int give_up = 0;
+      if ((threadIdx.x & 31) == 0) give_up = (abortable && aborted(hdr)) ? 1 : (globaltimer() - t0 > limit_ns) ? 2 : 0;
+      give_up = __shfl_sync(FULL, give_up, 0);
+      if (give_up) {
+        if (give_up == 2 && (threadIdx.x & 31) == 0) raise_status(hdr, ESC_ETIMEOUT);
+        return false;
+      }
     }
   }
+}
+
+// Warp-collective non-blocking test: true only if every lane observed it.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return __all_sync(FULL, ok != 0);
 }
 
 // ------------------------------------------------------------------ loads
@@ -226,72 +247,69 @@ __device__ __forceinline__ int64_t udf_rem(int64_t a, int64_t b, uint64_t d, uin
 
 // ------------------------------------------------------------------ evaluation
 // Runs the program on this lane's 8 rows of group `grp` of the staged tile.
-__device__ __forceinline__ uint32_t eval_group(const Query *__restrict__ Q, const uint8_t *stage, int grp,
-                                               int lane) {
+// Q (program included) lives in shared memory.
+__device__ __forceinline__ uint32_t eval_group(const Query *Q, const uint8_t *stage, int grp, int lane) {
   uint64_t S = 0;  // evaluation stack: entry k in bits [8k, 8k+8), top at bits 0..7
   const int n = Q->ninstr;
   for (int pc = 0; pc < n; ++pc) {
-    const Instr *I = &Q->code[pc];
-    const uint8_t op = I->op;
-    uint32_t m = 0;
-    if (op == OP_RANGE) {
-      const int dt = I->dtype;
-      const int w = width_of(dt);
-      const uint8_t *g = stage + Q->stage_off[I->ref] + (size_t)grp * kGroup * w;
-      if (dt == ESC_I64) {
-        int64_t v[8];
-        load8(dt, g, lane, v);
-        const int64_t lo = I->lo;
-        const uint64_t span = (uint64_t)I->hi - (uint64_t)lo;
+    const uint4 h = *reinterpret_cast<const uint4 *>(&Q->code[pc]);
+    const uint32_t op = h.x & 0xffu;
+    if (op <= OP_UDF) {
+      const longlong2 lh = *reinterpret_cast<const longlong2 *>(&Q->code[pc].lo);
+      const int dt = (int)((h.x >> 8) & 0xffu);
+      const uint32_t soff = h.z >> 16;
+      const uint8_t *g = stage + soff + (size_t)grp * kGroup * width_of(dt);
+      uint32_t m = 0;
+      if (op == OP_RANGE) {
+        if (dt == ESC_I64) {
+          int64_t v[8];
+          load8(dt, g, lane, v);
+          const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint64_t)v[k] - (uint64_t)lo <= span) << k;
-      } else {
-        int32_t v[8];
-        load8_32(dt, g, lane, v);
-        const int32_t lo = (int32_t)I->lo;
-        const uint32_t span = (uint32_t)((uint64_t)I->hi - (uint64_t)I->lo);
+          for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint64_t)v[k] - (uint64_t)lh.x <= span) << k;
+        } else {
+          int32_t v[8];
+          load8_32(dt, g, lane, v);
+          const uint32_t lo = (uint32_t)lh.x;
+          const uint32_t span = (uint32_t)((uint64_t)lh.y - (uint64_t)lh.x);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint32_t)v[k] - (uint32_t)lo <= span) << k;
-      }
-      S = (S << 8) | m;
-    } else if (op == OP_IN) {
-      const int dt = I->dtype;
-      const int w = width_of(dt);
-      const uint8_t *g = stage + Q->stage_off[I->ref] + (size_t)grp * kGroup * w;
-      const int64_t *vals = &Q->pool[I->off];
-      const int nv = I->n;
-      if (dt == ESC_I64) {
-        int64_t v[8];
-        load8(dt, g, lane, v);
-        for (int t = 0; t < nv; ++t) {
-          const int64_t c = vals[t];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+          for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint32_t)v[k] - lo <= span) << k;
         }
-      } else {
-        int32_t v[8];
-        load8_32(dt, g, lane, v);
-        for (int t = 0; t < nv; ++t) {
-          const int32_t c = (int32_t)vals[t];
+      } else if (op == OP_IN) {
+        const int64_t *vals = &Q->pool[h.z & 0xffffu];
+        const int nv = (int)(h.y >> 16);
+        if (dt == ESC_I64) {
+          int64_t v[8];
+          load8(dt, g, lane, v);
+          for (int t = 0; t < nv; ++t) {
+            const int64_t c = vals[t];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+            for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+          }
+        } else {
+          int32_t v[8];
+          load8_32(dt, g, lane, v);
+          for (int t = 0; t < nv; ++t) {
+            const int32_t c = (int32_t)vals[t];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+          }
         }
-      }
-      S = (S << 8) | m;
-    } else if (op == OP_UDF) {
-      int64_t a[8], b[8];
-      const int dt = I->dtype, dt2 = I->dtype2;
-      load8(dt, stage + Q->stage_off[I->ref] + (size_t)grp * kGroup * width_of(dt), lane, a);
-      load8(dt2, stage + Q->stage_off[I->ref2] + (size_t)grp * kGroup * width_of(dt2), lane, b);
-      const int64_t *P = &Q->pool[I->off];
-      const uint64_t d = (uint64_t)P[0], mult = (uint64_t)P[1];
-      const int sh1 = (int)P[2], sh2 = (int)P[3];
-      const int64_t lo = I->lo;
-      const uint64_t span = (uint64_t)I->hi - (uint64_t)lo;
+      } else {  // OP_UDF
+        const int dt2 = (int)((h.x >> 16) & 0xffu);
+        const uint32_t soff2 = h.w & 0xffffu;
+        int64_t a[8], b[8];
+        load8(dt, g, lane, a);
+        load8(dt2, stage + soff2 + (size_t)grp * kGroup * width_of(dt2), lane, b);
+        const int64_t *P = &Q->pool[h.z & 0xffffu];
+        const uint64_t d = (uint64_t)P[0], mult = (uint64_t)P[1];
+        const int sh1 = (int)P[2], sh2 = (int)P[3];
+        const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
-        m |= (uint32_t)((uint64_t)r - (uint64_t)lo <= span) << k;
+        for (int k = 0; k < 8; ++k) {
+          const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
+          m |= (uint32_t)((uint64_t)r - (uint64_t)lh.x <= span) << k;
+        }
       }
       S = (S << 8) | m;
     } else if (op == OP_AND) {
@@ -331,9 +349,8 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // by decoupled look-back (one warp).  Publishes the tile's aggregate first,
 // then its inclusive prefix.  Word = flag (bits 62..63: 1 aggregate,
 // 2 inclusive prefix) | value (bits 0..61).
-__device__ unsigned long long lookback(const Query *Q, uint32_t tile, unsigned long long total, int lane,
+__device__ unsigned long long lookback(unsigned long long *st, uint32_t tile, unsigned long long total, int lane,
                                        ScratchHdr *hdr) {
-  unsigned long long *st = Q->tile_status;
   const unsigned long long FA = 1ull << 62, FP = 2ull << 62, VM = FA - 1;
   if (tile == 0) {
     if (lane == 0) st_relaxed(&st[0], FP | total);
@@ -350,7 +367,7 @@ __device__ unsigned long long lookback(const Query *Q, uint32_t tile, unsigned l
     unsigned long long w = j >= 0 ? ld_relaxed(&st[j]) : FP;
     while (__any_sync(FULL, (w >> 62) == 0)) {
       if ((w >> 62) == 0) {
-        __nanosleep(40);
+        __nanosleep(20);
         w = ld_relaxed(&st[j]);
       }
       if ((++polls & 31u) == 0) {
@@ -379,29 +396,23 @@ __device__ unsigned long long lookback(const Query *Q, uint32_t tile, unsigned l
   return excl;
 }
 
-__device__ __forceinline__ void store_value(void *dst, uint64_t pos, const uint8_t *src, int w) {
-  switch (w) {
-    case 1: static_cast<uint8_t *>(dst)[pos] = *src; break;
-    case 2: static_cast<uint16_t *>(dst)[pos] = *reinterpret_cast<const uint16_t *>(src); break;
-    case 4: static_cast<uint32_t *>(dst)[pos] = *reinterpret_cast<const uint32_t *>(src); break;
-    default: static_cast<uint64_t *>(dst)[pos] = *reinterpret_cast<const uint64_t *>(src); break;
-  }
-}
-
 struct StageMeta {
   int32_t q;       // query index, -1 = end of work
   uint32_t tile;   // tile index within the query
   uint32_t rows;   // valid rows in this tile
-  uint32_t pad;
+  uint32_t dead;   // 1: the launch is aborting, skip the work (same for every reader)
+  uint32_t unit;   // unit index within the query
+  uint32_t useq;   // this CTA's running unit number (selects the unit buffer)
+  uint32_t first;  // first tile of its unit
+  uint32_t last;   // last tile of its unit
 };
 
 struct Launch {
   const Query *queries;  // device array of nq queries, or null: use q0
   int32_t nq;
-  uint32_t total_tiles;
+  uint32_t total_units;
   ScratchHdr *hdr;
-  uint32_t stage_bytes;
-  uint32_t pad;
+  uint32_t pad[4];
   Query q0;
 };
 
@@ -409,17 +420,167 @@ __device__ __forceinline__ const Query *query_ptr(const Launch &L, int q) {
   return L.queries ? &L.queries[q] : &L.q0;
 }
 
+// What the write-out of one compaction unit needs, copied out of the staged
+// query by the look-back warp (the stage may be reused before the write).
+struct UnitInfo {
+  unsigned long long excl;       // exclusive prefix of the unit's first row
+  uint64_t capacity;
+  uint32_t *out_ids;
+  const uint8_t *masks;
+  const uint32_t *gcounts;
+  unsigned int *tiles_left;
+  unsigned long long *done_ns;
+  uint32_t tile0, tile1;         // the unit's tiles [tile0, tile1)
+  uint32_t tile_rows, nrows, gmax;
+  int32_t nproj;
+  uint8_t proj_w[kMaxProj];
+  const uint8_t *proj_ptr[kMaxProj];
+  void *out_proj[kMaxProj];
+};
+
+// One projected column of a group: pass p covers the group's rows
+// 32p .. 32p+31 (lane = row); bal[p] is the pass's ballot of qualifying rows.
+template <typename T>
+__device__ __forceinline__ void sweep_column(const T *src, T *dst, unsigned long long base, uint64_t cap,
+                                             const uint32_t (&bal)[8], uint32_t selbits, uint32_t lt,
+                                             uint32_t row0) {
+  unsigned long long run = base;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    if ((selbits >> p) & 1u) {
+      const unsigned long long pos = run + __popc(bal[p] & lt);
+      if (pos < cap) dst[pos] = src[row0 + 32u * p];
+    }
+    run += __popc(bal[p]);
+  }
+}
+
+__device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned long long *done_ns, int lane) {
+  // Per-query completion time: every consumer warp retires each tile once.
+  if (done_ns && lane == 0) {
+    __threadfence();
+    if (atomicSub(tiles_left, 1u) == 1u) *done_ns = globaltimer();
+  }
+}
+
+// Writes this warp's share of a unit's qualifying rows: for every tile of the
+// unit in order, for the warp's groups, ids in ascending order and then each
+// projected column, at consecutive output slots after the unit's prefix.
+// Masks and group counts come from the scratch the evaluation wrote (L2);
+// projected values are re-read from the columns (the unit was streamed
+// through L2 moments ago).
+__device__ void write_unit(const UnitInfo *U, int cw, int lane) {
+  const uint64_t cap = U->capacity;
+  const int np = U->nproj;
+  const uint32_t lt = lanemask_lt();
+  unsigned long long running = U->excl;
+  for (uint32_t tile = U->tile0; tile < U->tile1; ++tile) {
+    const uint32_t r0 = tile * U->tile_rows;
+    const uint32_t rows = min(U->tile_rows, U->nrows - r0);
+    const int ngroups = (int)((rows + kGroup - 1) / kGroup);
+    const uint32_t *gc = U->gcounts + (size_t)tile * U->gmax;
+    // exclusive scan of the tile's group counts (<= 128: 4 per lane), same in every warp
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    const int gl = lane * 4;
+    if (gl < ngroups) c0 = __ldcg(gc + gl);
+    if (gl + 1 < ngroups) c1 = __ldcg(gc + gl + 1);
+    if (gl + 2 < ngroups) c2 = __ldcg(gc + gl + 2);
+    if (gl + 3 < ngroups) c3 = __ldcg(gc + gl + 3);
+    const uint32_t sum = c0 + c1 + c2 + c3;
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t e0 = inc - sum, e1 = e0 + c0, e2 = e1 + c1, e3 = e2 + c2;
+    const uint32_t tile_total = __shfl_sync(FULL, inc, 31);
+    if (tile_total != 0 && running < cap) {
+      for (int g = cw; g < ngroups; g += kConsumers) {
+        const int sub = g & 3;
+        const uint32_t cnt = __shfl_sync(FULL, sub == 0 ? c0 : sub == 1 ? c1 : sub == 2 ? c2 : c3, g >> 2);
+        if (cnt == 0) continue;
+        const uint32_t off = __shfl_sync(FULL, sub == 0 ? e0 : sub == 1 ? e1 : sub == 2 ? e2 : e3, g >> 2);
+        const unsigned long long base = running + off;
+        if (base >= cap) continue;
+        const uint8_t *mk = U->masks + ((size_t)tile * U->gmax + g) * 32;
+        const uint32_t m_even = __ldcg(mk + (lane >> 1));
+        const uint32_t m_odd = __ldcg(mk + 16 + (lane >> 1));
+        uint32_t bal[8];
+        uint32_t selbits = 0;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const uint32_t sel = (((p & 1) ? m_odd : m_even) >> (2 * (p >> 1) + (lane & 1))) & 1u;
+          bal[p] = __ballot_sync(FULL, sel);
+          selbits |= sel << p;
+        }
+        const uint32_t row0 = r0 + (uint32_t)g * kGroup + (uint32_t)lane;  // table row of pass 0
+        {
+          unsigned long long run = base;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            if ((selbits >> p) & 1u) {
+              const unsigned long long pos = run + __popc(bal[p] & lt);
+              if (pos < cap) U->out_ids[pos] = row0 + 32u * p;
+            }
+            run += __popc(bal[p]);
+          }
+        }
+        for (int c = 0; c < np; ++c) {
+          const int w = U->proj_w[c];
+          const uint8_t *src = U->proj_ptr[c];
+          void *dst = U->out_proj[c];
+          switch (w) {
+            case 1: sweep_column(src, static_cast<uint8_t *>(dst), base, cap, bal, selbits, lt, row0); break;
+            case 2:
+              sweep_column(reinterpret_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), base, cap, bal,
+                           selbits, lt, row0);
+              break;
+            case 4:
+              sweep_column(reinterpret_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), base, cap, bal,
+                           selbits, lt, row0);
+              break;
+            default:
+              sweep_column(reinterpret_cast<const unsigned long long *>(src),
+                           static_cast<unsigned long long *>(dst), base, cap, bal, selbits, lt, row0);
+              break;
+          }
+        }
+      }
+    }
+    running += tile_total;
+    retire_tile(U->tiles_left, U->done_ns, lane);
+  }
+}
+
+// Shared-memory layout of the scan kernel (offsets in bytes).
+struct SmemLayout {
+  static constexpr size_t stages = 0;
+  static constexpr size_t qslot = stages + (size_t)kStages * kStageBytes;
+  static constexpr size_t uinfo = qslot + (size_t)kStages * sizeof(Query);          // [2] UnitInfo
+  static constexpr size_t utotal = uinfo + 2 * ((sizeof(UnitInfo) + 15) & ~(size_t)15);  // [2] u64
+  static constexpr size_t bars = utotal + 16;           // full[S] empty[S] uevald[2] uready[2]
+  static constexpr size_t meta = bars + (2 * kStages + 4) * 8;
+  static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);                // [S] int32
+  static constexpr size_t total = slotq + kStages * 4;
+};
+
 // ------------------------------------------------------------------ the kernel
+// Warp 0: producer (unit tickets, bulk copies).  Warp 1: look-back (unit
+// prefixes for ordered compaction).  Warps 2..: consumers (evaluate, count,
+// write).
 __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *stages = smem;
-  uint64_t *full_bar = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * L.stage_bytes);
+  uint8_t *stages = smem + SmemLayout::stages;
+  Query *qslot = reinterpret_cast<Query *>(smem + SmemLayout::qslot);
+  UnitInfo *uinfo = reinterpret_cast<UnitInfo *>(smem + SmemLayout::uinfo);
+  unsigned long long *utotal = reinterpret_cast<unsigned long long *>(smem + SmemLayout::utotal);
+  uint64_t *full_bar = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
   uint64_t *empty_bar = full_bar + kStages;
-  StageMeta *meta = reinterpret_cast<StageMeta *>(empty_bar + kStages);
-  uint8_t *masks = reinterpret_cast<uint8_t *>(meta + kStages);                 // kMaxGroups * 32
-  uint32_t *gcnt = reinterpret_cast<uint32_t *>(masks + kMaxGroups * 32);       // kMaxGroups
-  unsigned long long *gofs = reinterpret_cast<unsigned long long *>(gcnt + kMaxGroups);  // kMaxGroups
-  unsigned long long *tile_excl = gofs + kMaxGroups;
+  uint64_t *uevald_bar = empty_bar + kStages;
+  uint64_t *uready_bar = uevald_bar + 2;
+  StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SmemLayout::meta);
+  int32_t *slotq = reinterpret_cast<int32_t *>(smem + SmemLayout::slotq);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -428,7 +589,13 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], kConsumers);
+      mbar_init(&empty_bar[s], kConsumers + 1);
+      slotq[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&uevald_bar[b], kConsumers);
+      mbar_init(&uready_bar[b], 1);
+      utotal[b] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -437,64 +604,168 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     int s = 0;
-    uint32_t phase = 0;
+    uint32_t phase = 0, useq = 0;
     int qc = 0;  // cursor over queries: tickets of one CTA only increase
-    while (true) {
-      uint32_t t = 0;
-      if (lane == 0) t = atomicAdd(&hdr->ticket, 1u);
-      t = __shfl_sync(FULL, t, 0);
-      const bool stop = t >= L.total_tiles || aborted(hdr);
-      if (!mbar_wait(&empty_bar[s], phase ^ 1u, hdr)) break;
-      if (stop) {
-        if (lane == 0) {
+    bool done = false;
+    while (!done) {
+      uint32_t u = 0;
+      if (lane == 0) u = atomicAdd(&hdr->ticket, 1u);
+      u = __shfl_sync(FULL, u, 0);
+      if (u >= L.total_units || aborted(hdr)) {
+        if (mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true) && lane == 0) {
           meta[s].q = -1;
           mbar_arrive(&full_bar[s]);
         }
         break;
       }
-      while (qc + 1 < L.nq) {
-        const Query *nq = query_ptr(L, qc + 1);
-        if (t >= nq->tile_base) ++qc; else break;
-      }
-      const Query *Q = query_ptr(L, qc);
-      const uint32_t tile = t - Q->tile_base;
-      const uint32_t r0 = tile * Q->tile_rows;
-      const uint32_t rows = min(Q->tile_rows, Q->nrows - r0);
-      uint8_t *stage = stages + (size_t)s * L.stage_bytes;
-      // bytes of each read column: a 16-byte multiple by bulk copy, the rest by hand
-      uint32_t bulk = 0, tail = 0;
-      const uint8_t *src = nullptr;
-      uint8_t *dst = nullptr;
-      if (lane < Q->nref) {
-        const uint32_t w = Q->ref_w[lane];
-        const uint32_t bytes = rows * w;
-        bulk = bytes & ~15u;
-        tail = bytes - bulk;
-        src = Q->ref_ptr[lane] + (size_t)r0 * w;
-        dst = stage + Q->stage_off[lane];
-      }
-      uint32_t any_tail = __ballot_sync(FULL, tail != 0);
-      if (any_tail) {
-        for (int c = 0; c < Q->nref; ++c) {
-          const uint32_t tb = __shfl_sync(FULL, tail, c);
-          const uint32_t bb = __shfl_sync(FULL, bulk, c);
-          const uint8_t *sp = reinterpret_cast<const uint8_t *>(__shfl_sync(FULL, (unsigned long long)src, c));
-          uint8_t *dp = reinterpret_cast<uint8_t *>(__shfl_sync(FULL, (unsigned long long)dst, c));
-          if ((uint32_t)lane < tb) dp[bb + lane] = sp[bb + lane];
+      while (qc + 1 < L.nq && u >= query_ptr(L, qc + 1)->unit_base) ++qc;
+      const Query *Qg = query_ptr(L, qc);
+      const uint32_t unit = u - Qg->unit_base;
+      const uint32_t ut = Qg->unit_tiles;
+      const uint32_t t0 = unit * ut;
+      const uint32_t t1 = min(t0 + ut, Qg->ntiles);
+      for (uint32_t tile = t0; tile < t1; ++tile) {
+        if (!mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true)) {
+          done = true;
+          break;
         }
-        fence_proxy_async_smem();
+        Query *Q = &qslot[s];
+        if (slotq[s] != qc) {  // stage the query (program included) in shared memory
+          const uint2 *src = reinterpret_cast<const uint2 *>(Qg);
+          uint2 *dst = reinterpret_cast<uint2 *>(Q);
+          for (int i = lane; i < (int)(sizeof(Query) / 8); i += 32) dst[i] = src[i];
+          __syncwarp();
+          if (lane == 0) slotq[s] = qc;
+        }
+        __syncwarp();
+        const uint32_t r0 = tile * Q->tile_rows;
+        const uint32_t rows = min(Q->tile_rows, Q->nrows - r0);
+        uint8_t *stage = stages + (size_t)s * kStageBytes;
+        // bytes of each read column: a 16-byte multiple by bulk copy, the rest by hand
+        uint32_t bulk = 0, tail = 0;
+        const uint8_t *src = nullptr;
+        uint8_t *dst = nullptr;
+        const int nref = Q->nref;
+        if (lane < nref) {
+          const uint32_t w = Q->ref_w[lane];
+          const uint32_t bytes = rows * w;
+          bulk = bytes & ~15u;
+          tail = bytes - bulk;
+          src = Q->ref_ptr[lane] + (size_t)r0 * w;
+          dst = stage + Q->stage_off[lane];
+        }
+        if (__ballot_sync(FULL, tail != 0)) {
+          for (int c = 0; c < nref; ++c) {
+            const uint32_t tb = __shfl_sync(FULL, tail, c);
+            const uint32_t bb = __shfl_sync(FULL, bulk, c);
+            const uint8_t *sp = reinterpret_cast<const uint8_t *>(__shfl_sync(FULL, (unsigned long long)src, c));
+            uint8_t *dp = reinterpret_cast<uint8_t *>(__shfl_sync(FULL, (unsigned long long)dst, c));
+            if ((uint32_t)lane < tb) dp[bb + lane] = sp[bb + lane];
+          }
+          fence_proxy_async_smem();
+        }
+        const unsigned long long tot = warp_sum(bulk);
+        __syncwarp();
+        if (lane == 0) {
+          StageMeta &m = meta[s];
+          m.q = qc;
+          m.tile = tile;
+          m.rows = rows;
+          m.dead = aborted(hdr) ? 1u : 0u;
+          m.unit = unit;
+          m.useq = useq;
+          m.first = tile == t0;
+          m.last = tile + 1 == t1;
+          mbar_arrive_expect_tx(&full_bar[s], (uint32_t)tot);
+        }
+        __syncwarp();
+        if (bulk) bulk_load(dst, src, bulk, &full_bar[s]);
+        if (++s == kStages) {
+          s = 0;
+          phase ^= 1u;
+        }
       }
-      unsigned long long tot = bulk;
-      tot = warp_sum(tot);
-      __syncwarp();
-      if (lane == 0) {
-        meta[s].q = qc;
-        meta[s].tile = tile;
-        meta[s].rows = rows;
-        mbar_arrive_expect_tx(&full_bar[s], (uint32_t)tot);
+      ++useq;
+    }
+    return;
+  }
+
+  if (warp == 1) {
+    // ---------------------------------------------------------------- look-back
+    int s = 0;
+    uint32_t phase = 0, evp = 0;  // evp bit b: parity of uevald_bar[b]
+    while (true) {
+      if (!mbar_wait(&full_bar[s], phase, hdr)) break;
+      const StageMeta mt = meta[s];
+      if (mt.q < 0) break;
+      const Query *Q = &qslot[s];
+      const bool unit_end = Q->mode == MODE_COMPACT && mt.last;
+      const uint32_t b = mt.useq & 1u;
+      // Copy what the write-out needs into registers before the stage is
+      // released; publish it only after every consumer has evaluated this
+      // unit, i.e. has finished writing the unit that last used buffer b.
+      unsigned long long *status = nullptr, *count = nullptr;
+      UnitInfo r;  // lane 0: scalars; lane c < nproj: column c
+      uint8_t pw = 0;
+      const uint8_t *pp = nullptr;
+      void *po = nullptr;
+      int nproj = 0;
+      if (unit_end) {
+        r.capacity = Q->capacity;
+        r.out_ids = Q->out_ids;
+        r.masks = Q->masks;
+        r.gcounts = Q->gcounts;
+        r.tiles_left = Q->tiles_left;
+        r.done_ns = Q->done_ns;
+        r.tile0 = mt.unit * Q->unit_tiles;
+        r.tile1 = mt.tile + 1;
+        r.tile_rows = Q->tile_rows;
+        r.nrows = Q->nrows;
+        r.gmax = Q->gmax;
+        nproj = Q->nproj;
+        if (lane < nproj) {
+          pw = Q->proj_w[lane];
+          pp = Q->proj_ptr[lane];
+          po = Q->out_proj[lane];
+        }
+        status = Q->unit_status;
+        count = Q->count;
       }
       __syncwarp();
-      if (bulk) bulk_load(dst, src, bulk, &full_bar[s]);
+      if (lane == 0) mbar_arrive(&empty_bar[s]);
+      if (unit_end) {
+        mbar_wait(&uevald_bar[b], (evp >> b) & 1u, hdr, 2 * kWaitLimitNs, true);
+        evp ^= 1u << b;
+        const unsigned long long total = utotal[b];
+        const unsigned long long excl = mt.dead ? 0ull : lookback(status, mt.unit, total, lane, hdr);
+        UnitInfo *U = &uinfo[b];
+        if (lane < nproj) {
+          U->proj_w[lane] = pw;
+          U->proj_ptr[lane] = pp;
+          U->out_proj[lane] = po;
+        }
+        if (lane == 0) {
+          r.excl = excl;
+          r.nproj = nproj;
+          U->excl = r.excl;
+          U->capacity = r.capacity;
+          U->out_ids = r.out_ids;
+          U->masks = r.masks;
+          U->gcounts = r.gcounts;
+          U->tiles_left = r.tiles_left;
+          U->done_ns = r.done_ns;
+          U->tile0 = r.tile0;
+          U->tile1 = r.tile1;
+          U->tile_rows = r.tile_rows;
+          U->nrows = r.nrows;
+          U->gmax = r.gmax;
+          U->nproj = r.nproj;
+          utotal[b] = 0;
+          if (total) atomicAdd(count, total);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&uready_bar[b]);
+      }
       if (++s == kStages) {
         s = 0;
         phase ^= 1u;
@@ -504,30 +775,32 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   }
 
   // ---------------------------------------------------------------- consumers
-  const int cw = warp - 1;
+  const int cw = warp - 2;
   int s = 0;
-  uint32_t phase = 0;
+  uint32_t phase = 0, rdp = 0;  // rdp bit b: parity of uready_bar[b]
+  int npend = 0;                // compaction units evaluated but not yet written (<= 2)
+  uint32_t pend_head = 0;       // unit buffer of the oldest pending unit
   while (true) {
     if (!mbar_wait(&full_bar[s], phase, hdr)) break;
     const StageMeta mt = meta[s];
     if (mt.q < 0) break;
-    const Query *Q = query_ptr(L, mt.q);
-    const uint8_t *stage = stages + (size_t)s * L.stage_bytes;
+    const Query *Q = &qslot[s];
+    const uint8_t *stage = stages + (size_t)s * kStageBytes;
     const uint32_t rows = mt.rows;
     const int ngroups = (int)((rows + kGroup - 1) / kGroup);
     const int mode = Q->mode;
     const uint32_t r0 = mt.tile * Q->tile_rows;
-    const bool dead = aborted(hdr);
-
+    const bool dead = mt.dead != 0;
     if (mode == MODE_COUNT) {
       uint32_t cnt = 0;
       if (!dead)
-        for (int g = cw; g < ngroups; g += kConsumers) {
-          uint32_t m = eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows);
-          cnt += __popc(m);
-        }
+        for (int g = cw; g < ngroups; g += kConsumers)
+          cnt += __popc(eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
       const unsigned long long tot = warp_sum(cnt);
       if (lane == 0 && tot) atomicAdd(Q->count, tot);
+      retire_tile(Q->tiles_left, Q->done_ns, lane);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[s]);
     } else if (mode == MODE_BITMAP) {
       uint32_t cnt = 0;
       const uint32_t nwords = (Q->nrows + 31u) / 32u;
@@ -540,100 +813,66 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           for (int p = 0; p < 8; ++p) {
             const int src = 16 * (p & 1) + (lane >> 1);
             const int bit = 2 * (p >> 1) + (lane & 1);
-            const uint32_t b = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
-            if (lane == p) word = b;
+            const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
+            if (lane == p) word = bb;
           }
           const uint32_t wi = (r0 + (uint32_t)g * kGroup) / 32u + (uint32_t)lane;
           if (lane < 8 && wi < nwords) Q->bitmap[wi] = word;
         }
       const unsigned long long tot = warp_sum(cnt);
       if (lane == 0 && tot) atomicAdd(Q->count, tot);
-    } else {  // MODE_COMPACT
+      retire_tile(Q->tiles_left, Q->done_ns, lane);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[s]);
+    } else {  // MODE_COMPACT: evaluate into the mask scratch; the unit is written later
+      const uint32_t b = mt.useq & 1u;
+      // Buffer b may still be held by an older pending unit: write pending
+      // units out, oldest first, until none of them uses b.
+      while (mt.first && npend > 0 && (npend == 2 || pend_head == b)) {
+        const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
+        rdp ^= 1u << pend_head;
+        if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+        pend_head ^= 1u;
+        --npend;
+      }
+      uint32_t cnt = 0;
+      uint8_t *mk = Q->masks + (size_t)mt.tile * Q->gmax * 32;
+      uint32_t *gc = Q->gcounts + (size_t)mt.tile * Q->gmax;
       for (int g = cw; g < ngroups; g += kConsumers) {
-        uint32_t m = dead ? 0u : (eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
-        masks[g * 32 + lane] = (uint8_t)m;
-        const unsigned long long c = warp_sum(__popc(m));
-        if (lane == 0) gcnt[g] = (uint32_t)c;
+        const uint32_t m = dead ? 0u : (eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
+        mk[g * 32 + lane] = (uint8_t)m;
+        const uint32_t c = (uint32_t)warp_sum(__popc(m));
+        if (lane == 0) gc[g] = c;
+        cnt += c;
       }
-      consumer_sync();
-      if (cw == 0) {
-        // exclusive scan of the group counts (<= 128 groups: 4 per lane)
-        unsigned long long loc[4], sum = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int g = lane * 4 + k;
-          loc[k] = g < ngroups ? gcnt[g] : 0;
-          sum += loc[k];
-        }
-        unsigned long long inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long y = __shfl_up_sync(FULL, inc, o);
-          if (lane >= o) inc += y;
-        }
-        unsigned long long run = inc - sum;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int g = lane * 4 + k;
-          if (g < ngroups) gofs[g] = run;
-          run += loc[k];
-        }
-        const unsigned long long total = __shfl_sync(FULL, inc, 31);
-        const unsigned long long excl = lookback(Q, mt.tile, total, lane, hdr);
-        if (lane == 0) {
-          *tile_excl = excl;
-          if (total) atomicAdd(Q->count, total);
-        }
-      }
-      consumer_sync();
-      if (!aborted(hdr)) {
-        const unsigned long long texcl = *tile_excl;
-        const uint64_t cap = Q->capacity;
-        const int np = Q->nproj;
-        for (int g = cw; g < ngroups; g += kConsumers) {
-          if (gcnt[g] == 0) continue;
-          unsigned long long base = texcl + gofs[g];
-          if (base >= cap) continue;
-#pragma unroll 1
-          for (int p = 0; p < 8; ++p) {
-            const int src = 16 * (p & 1) + (lane >> 1);
-            const int bit = 2 * (p >> 1) + (lane & 1);
-            const uint32_t sel = (masks[g * 32 + src] >> bit) & 1u;
-            const uint32_t b = __ballot_sync(FULL, sel);
-            if (b == 0) continue;
-            if (sel) {
-              const unsigned long long pos = base + __popc(b & lanemask_lt());
-              if (pos < cap) {
-                const uint32_t rt = (uint32_t)g * kGroup + (uint32_t)p * 32u + (uint32_t)lane;
-                Q->out_ids[pos] = r0 + rt;
-                for (int c = 0; c < np; ++c) {
-                  const int w = Q->proj_w[c];
-                  const int rf = Q->proj_ref[c];
-                  const uint8_t *sp = rf >= 0 ? stage + Q->stage_off[rf] + (size_t)rt * w
-                                              : Q->proj_ptr[c] + (size_t)(r0 + rt) * w;
-                  store_value(Q->out_proj[c], pos, sp, w);
-                }
-              }
-            }
-            base += __popc(b);
-          }
-        }
+      if (lane == 0 && cnt) atomicAdd(&utotal[b], (unsigned long long)cnt);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[s]);
+      if (mt.last) {
+        __threadfence_block();
+        if (lane == 0) mbar_arrive(&uevald_bar[b]);
+        if (npend == 0) pend_head = b;
+        ++npend;
       }
     }
-
-    if (Q->done_ns) {
-      consumer_sync();
-      if (cw == 0 && lane == 0) {
-        __threadfence();
-        if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
-      }
+    // write out the oldest evaluated unit once its prefix is known
+    if (npend > 0 && mbar_test(&uready_bar[pend_head], (rdp >> pend_head) & 1u)) {
+      rdp ^= 1u << pend_head;
+      if (!aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+      pend_head ^= 1u;
+      --npend;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty_bar[s]);
     if (++s == kStages) {
       s = 0;
       phase ^= 1u;
     }
+  }
+  while (npend > 0) {  // drain
+    const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
+    rdp ^= 1u << pend_head;
+    if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+    pend_head ^= 1u;
+    --npend;
   }
 }
 
@@ -661,10 +900,7 @@ struct DeviceState {
 };
 DeviceState g_dev[64];
 
-size_t smem_bytes() {
-  return (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(StageMeta) +
-         kMaxGroups * 32 + kMaxGroups * 4 + kMaxGroups * 8 + 16;
-}
+size_t smem_bytes() { return SmemLayout::total; }
 
 #define ESC_CK(call)                                                                      \
   do {                                                                                    \
@@ -701,27 +937,47 @@ esc_status device_state(DeviceState **out) {
 }
 
 // Tile size for a query: as many rows as fit in one stage, a multiple of the
-// CTA's rows per sweep (kConsumers groups) when possible, else of one group.
+// 256-row group, at most kMaxTileRows.
 uint32_t tile_rows_for(const Query &q) {
   uint32_t bpr = 0;
   for (int i = 0; i < q.nref; ++i) bpr += q.ref_w[i];
   if (bpr == 0) bpr = 1;
-  uint32_t t = kStageBytes / bpr;
-  const uint32_t sweep = kGroup * kConsumers;
-  t = t >= sweep ? (t / sweep) * sweep : (t / kGroup) * kGroup;
+  uint32_t t = (kStageBytes / bpr / kGroup) * kGroup;
   t = std::max<uint32_t>(t, kGroup);
   return std::min<uint32_t>(t, kMaxTileRows);
 }
 
-// Stage layout: read columns back to back, each slice 128-byte aligned.
-void layout_stage(Query &q) {
+// Stage layout (read columns back to back, each slice 128-byte aligned), and
+// the work units: consecutive tiles claimed with one ticket and, for ordered
+// compaction, resolved with one look-back.  Units hold at most ~512 KB of
+// staged columns and there are >= 8 per SM when the table is large enough,
+// which keeps the unit rate (look-backs per microsecond) low enough for the
+// look-back chain to keep up with HBM.
+void layout_stage(Query &q, int sms) {
   q.tile_rows = tile_rows_for(q);
-  uint32_t off = 0;
+  uint32_t off = 0, bpr = 0;
   for (int i = 0; i < q.nref; ++i) {
     q.stage_off[i] = off;
     off += (q.tile_rows * q.ref_w[i] + 127u) & ~127u;
+    bpr += q.ref_w[i];
+  }
+  for (int pc = 0; pc < q.ninstr; ++pc) {  // resolve operand slots to stage offsets
+    Instr &I = q.code[pc];
+    if (I.op == OP_RANGE || I.op == OP_IN || I.op == OP_UDF) I.soff = (uint16_t)q.stage_off[I.ref];
+    if (I.op == OP_UDF) I.soff2 = (uint16_t)q.stage_off[I.ref2];
   }
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;
+  q.gmax = q.tile_rows / kGroup;
+  const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);
+  const uint32_t max_ut = (uint32_t)std::max<uint64_t>(1, (512ull * 1024) / tile_bytes);
+  const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * 8);
+  q.unit_tiles = std::min(std::max<uint32_t>(want, 1), max_ut);
+  q.nunits = (q.ntiles + q.unit_tiles - 1) / q.unit_tiles;
+}
+
+// Bytes of device scratch a compaction query needs after its look-back words.
+size_t compact_scratch_bytes(const Query &q) {
+  return (size_t)q.ntiles * q.gmax * 32 + (size_t)q.ntiles * q.gmax * 4;
 }
 
 esc_status alloc_async(void **p, size_t bytes, cudaStream_t st) {
@@ -737,9 +993,9 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
   DeviceState *d;
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
-  if (L.total_tiles == 0) return ESC_OK;
+  if (L.total_units == 0) return ESC_OK;
   const uint32_t cap = (uint32_t)(d->sms * d->blocks_per_sm);
-  const uint32_t grid = std::min<uint32_t>(cap, L.total_tiles);
+  const uint32_t grid = std::min<uint32_t>(cap, L.total_units);
   scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
@@ -748,6 +1004,9 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
 // Validates a (table, pred, rows) call and fills the per-call query.
 esc_status prepare_query(const esc_table *t, const esc_pred *p, const esc_rows *rows, int mode, Query *q) {
   if (!t || !p) return fail(ESC_EINVAL, "table and predicate are required");
+  DeviceState *d;
+  esc_status ds = device_state(&d);
+  if (ds != ESC_OK) return ds;
   if (p->table != t) return fail(ESC_EINVAL, "predicate was compiled against another table");
   std::memset(q, 0, sizeof *q);
   fill_query_program(p, q);
@@ -764,7 +1023,7 @@ esc_status prepare_query(const esc_table *t, const esc_pred *p, const esc_rows *
       if (rows->capacity && !q->out_proj[i]) return fail(ESC_EINVAL, "a projected output pointer is NULL");
     }
   }
-  layout_stage(*q);
+  layout_stage(*q, d->sms);
   return ESC_OK;
 }
 
@@ -790,27 +1049,28 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   if (s != ESC_OK) return s;
   L.q0.bitmap = bitmap;
   L.nq = 1;
-  L.total_tiles = L.q0.ntiles;
-  L.stage_bytes = kStageBytes;
-  const size_t status_bytes = mode == MODE_COMPACT ? (size_t)L.q0.ntiles * 8 : 0;
-  const size_t bytes = sizeof(SingleScratch) + status_bytes;
+  L.total_units = L.q0.nunits;
+  // scratch: header + count, then (compaction) look-back words (zeroed), masks, group counts
+  const size_t head = (sizeof(SingleScratch) + 255) & ~(size_t)255;
+  const size_t status_bytes = mode == MODE_COMPACT ? (((size_t)L.q0.nunits * 8 + 255) & ~(size_t)255) : 0;
+  const size_t extra = mode == MODE_COMPACT ? compact_scratch_bytes(L.q0) : 0;
+  const size_t bytes = head + status_bytes + extra;
   void *mem = nullptr;
   if ((s = alloc_async(&mem, bytes, st)) != ESC_OK) return s;
-  cudaError_t e = cudaMemsetAsync(mem, 0, bytes, st);
+  cudaError_t e = cudaMemsetAsync(mem, 0, head + status_bytes, st);
+  if (e == cudaSuccess && dev_count) e = cudaMemsetAsync(dev_count, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, st);
     return fail(ESC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   }
+  uint8_t *base = static_cast<uint8_t *>(mem);
   SingleScratch *sc = static_cast<SingleScratch *>(mem);
   L.hdr = &sc->hdr;
   L.q0.count = dev_count ? dev_count : &sc->count;
-  L.q0.tile_status = mode == MODE_COMPACT ? reinterpret_cast<unsigned long long *>(sc + 1) : nullptr;
-  if (dev_count) {
-    e = cudaMemsetAsync(dev_count, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) {
-      cudaFreeAsync(mem, st);
-      return fail(ESC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    }
+  if (mode == MODE_COMPACT) {
+    L.q0.unit_status = reinterpret_cast<unsigned long long *>(base + head);
+    L.q0.masks = base + head + status_bytes;
+    L.q0.gcounts = reinterpret_cast<uint32_t *>(base + head + status_bytes + (size_t)L.q0.ntiles * L.q0.gmax * 32);
   }
   s = launch_scan(L, st);
   if (s != ESC_OK) {
@@ -892,7 +1152,7 @@ esc_status esc_bitmap_build(const esc_table *dim, const esc_pred *p, uint32_t *d
 struct esc_batch {
   int32_t n = 0;
   int device = 0;
-  uint32_t total_tiles = 0;
+  uint32_t total_units = 0;
   void *dev_mem = nullptr;          // queries + scratch, owned
   Query *queries = nullptr;         // device
   uint8_t *scratch = nullptr;       // device: hdr, counts, done, tiles_left, look-back words
@@ -928,29 +1188,34 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
-  uint64_t tiles = 0, status_words = 0;
+  uint64_t units = 0, status_words = 0, extra_bytes = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_COMPACT : MODE_COUNT,
                            &qs[i])) != ESC_OK)
       return s;
-    qs[i].tile_base = (uint32_t)tiles;
-    tiles += qs[i].ntiles;
-    if (compact) status_words += qs[i].ntiles;
-    if (tiles >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many tiles in one batch");
+    qs[i].unit_base = (uint32_t)units;
+    units += qs[i].nunits;
+    if (compact) {
+      status_words += qs[i].nunits;
+      extra_bytes += (compact_scratch_bytes(qs[i]) + 255) & ~(uint64_t)255;
+    }
+    if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
   }
   esc_batch *b = new (std::nothrow) esc_batch;
   if (!b) return fail(ESC_ENOMEM, "esc_batch_prepare: out of host memory");
   b->n = n;
   cudaGetDevice(&b->device);
-  b->total_tiles = (uint32_t)tiles;
+  b->total_units = (uint32_t)units;
   const size_t q_bytes = sizeof(Query) * (size_t)n;
   const size_t hdr_bytes = 256;
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
-  b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + status_words * 8;
-  const size_t total = q_bytes + b->scratch_bytes + left_bytes;
+  b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + status_words * 8;  // zeroed every run
+  const size_t q_span = (q_bytes + 255) & ~(size_t)255;
+  const size_t work_span = (size_t)extra_bytes;                                   // masks, group counts
+  const size_t total = q_span + b->scratch_bytes + left_bytes + 256 + work_span;
   cudaError_t e = cudaMalloc(&b->dev_mem, total);
   if (e != cudaSuccess) {
     batch_free(b);
@@ -958,27 +1223,35 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   }
   uint8_t *base = static_cast<uint8_t *>(b->dev_mem);
   b->queries = reinterpret_cast<Query *>(base);
-  b->scratch = base + ((q_bytes + 255) & ~(size_t)255);
+  b->scratch = base + q_span;
   b->counts = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes);
   b->done = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes + cnt_bytes);
   b->tiles_left = reinterpret_cast<unsigned int *>(b->scratch + hdr_bytes + 2 * cnt_bytes);
   unsigned long long *status = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes + 2 * cnt_bytes + left_bytes);
   b->tiles_init = reinterpret_cast<unsigned int *>(b->scratch + b->scratch_bytes);
-  if (((uintptr_t)b->tiles_init + left_bytes) > (uintptr_t)base + total + 256) {
+  if (((uintptr_t)b->tiles_init + left_bytes) > (uintptr_t)base + total) {
     batch_free(b);
     return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
   }
   std::vector<unsigned int> init((size_t)n);
   uint64_t so = 0;
+  uint8_t *work = reinterpret_cast<uint8_t *>(((uintptr_t)b->tiles_init + left_bytes + 255) & ~(uintptr_t)255);
   for (int i = 0; i < n; ++i) {
     qs[i].count = &b->counts[i];
     qs[i].done_ns = &b->done[i];
     qs[i].tiles_left = &b->tiles_left[i];
     if (qs[i].mode == MODE_COMPACT) {
-      qs[i].tile_status = status + so;
-      so += qs[i].ntiles;
+      qs[i].unit_status = status + so;
+      so += qs[i].nunits;
+      qs[i].masks = work;
+      qs[i].gcounts = reinterpret_cast<uint32_t *>(work + (size_t)qs[i].ntiles * qs[i].gmax * 32);
+      work += (compact_scratch_bytes(qs[i]) + 255) & ~(size_t)255;
     }
-    init[i] = qs[i].ntiles;
+    init[i] = qs[i].ntiles * (unsigned)kConsumers;
+  }
+  if ((uintptr_t)work > (uintptr_t)base + total) {
+    batch_free(b);
+    return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
   }
   e = cudaMemcpy(b->queries, qs.data(), q_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->tiles_init, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
@@ -997,9 +1270,8 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   std::memset(&L, 0, sizeof L);
   L.queries = b->queries;
   L.nq = n;
-  L.total_tiles = b->total_tiles;
+  L.total_units = b->total_units;
   L.hdr = reinterpret_cast<ScratchHdr *>(b->scratch);
-  L.stage_bytes = kStageBytes;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   esc_status ls = ESC_OK;
   if (e == cudaSuccess) {

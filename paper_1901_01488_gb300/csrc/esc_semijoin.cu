@@ -76,7 +76,7 @@ __device__ __forceinline__ void flush(uint64_t &lo, uint64_t &hi, uint32_t (&c)[
 }
 
 template <int ND>
-__global__ void __launch_bounds__(kSjThreads) semijoin_kernel(const __grid_constant__ SjParams P) {
+__global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_constant__ SjParams P) {
   extern __shared__ __align__(16) uint32_t sbm[];
   __shared__ unsigned long long bins[16];
   for (int d = 0; d < ND; ++d) {
