@@ -24,6 +24,7 @@ constexpr int kMaxDepth = 8;    // evaluation stack: 8 masks of 8 bits in one u6
 constexpr int kV = 8;           // rows per lane per group
 constexpr int kGroup = 256;     // rows per warp group (32 lanes x 8 rows)
 constexpr int kMaxTileRows = 32768;
+constexpr int kMaxUnitRows = 65536;   // rows per work unit (its masks stay in shared memory)
 
 // Lane l of a warp owns, in a 256-row group, the rows
 //   64*j + 2*l + i   for j in 0..3, i in 0..1;
@@ -90,8 +91,6 @@ struct Query {
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
   unsigned long long *unit_status;// decoupled look-back words, one per unit (zeroed)
-  uint8_t *masks;                 // compaction scratch: 32 bytes per group (ntiles x gmax groups)
-  uint32_t *gcounts;              // compaction scratch: qualifying rows per group
   unsigned int *tiles_left;       // consumer-warp tile visits left (ntiles x warps, set before launch)
   unsigned long long *done_ns;    // %globaltimer when the last tile finished (may be null)
   Instr code[kMaxInstr];

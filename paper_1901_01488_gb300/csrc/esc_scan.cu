@@ -36,10 +36,11 @@
 
 namespace esc {
 
-constexpr int kConsumers = 16;                   // consumer warps per CTA
+constexpr int kConsumers = 14;                   // consumer warps per CTA (16 warps in all: 4 per SM sub-partition)
 constexpr int kThreads = 32 * (kConsumers + 2);  // + producer warp + look-back warp
 constexpr int kStages = 4;
-constexpr uint32_t kStageBytes = 48 * 1024;
+constexpr uint32_t kStageBytes = 44 * 1024;
+constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr uint32_t FULL = 0xffffffffu;
 static_assert(kStageBytes <= 65536, "stage offsets are 16-bit");
@@ -426,8 +427,6 @@ struct UnitInfo {
   unsigned long long excl;       // exclusive prefix of the unit's first row
   uint64_t capacity;
   uint32_t *out_ids;
-  const uint8_t *masks;
-  const uint32_t *gcounts;
   unsigned int *tiles_left;
   unsigned long long *done_ns;
   uint32_t tile0, tile1;         // the unit's tiles [tile0, tile1)
@@ -438,22 +437,14 @@ struct UnitInfo {
   void *out_proj[kMaxProj];
 };
 
-// One projected column of a group: pass p covers the group's rows
-// 32p .. 32p+31 (lane = row); bal[p] is the pass's ballot of qualifying rows.
-template <typename T>
-__device__ __forceinline__ void sweep_column(const T *src, T *dst, unsigned long long base, uint64_t cap,
-                                             const uint32_t (&bal)[8], uint32_t selbits, uint32_t lt,
-                                             uint32_t row0) {
-  unsigned long long run = base;
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    if ((selbits >> p) & 1u) {
-      const unsigned long long pos = run + __popc(bal[p] & lt);
-      if (pos < cap) dst[pos] = src[row0 + 32u * p];
-    }
-    run += __popc(bal[p]);
-  }
-}
+// Per-unit compaction state in shared memory (two buffers, alternating
+// units): each evaluated group's 8-bit lane masks (32 bytes), its count of
+// qualifying rows, and its exclusive offset within the unit.
+struct UnitBuf {
+  uint8_t masks[kMaxUnitGroups * 32];
+  uint32_t gcnt[kMaxUnitGroups];
+  uint32_t gofs[kMaxUnitGroups];
+};
 
 __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned long long *done_ns, int lane) {
   // Per-query completion time: every consumer warp retires each tile once.
@@ -463,92 +454,93 @@ __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned l
   }
 }
 
+__device__ __forceinline__ uint64_t load_elem(const uint8_t *base, uint32_t row, int w) {
+  switch (w) {
+    case 1: return base[row];
+    case 2: return reinterpret_cast<const uint16_t *>(base)[row];
+    case 4: return reinterpret_cast<const uint32_t *>(base)[row];
+    default: return reinterpret_cast<const unsigned long long *>(base)[row];
+  }
+}
+
+__device__ __forceinline__ void store_elem(void *base, unsigned long long pos, uint64_t v, int w) {
+  switch (w) {
+    case 1: static_cast<uint8_t *>(base)[pos] = (uint8_t)v; break;
+    case 2: static_cast<uint16_t *>(base)[pos] = (uint16_t)v; break;
+    case 4: static_cast<uint32_t *>(base)[pos] = (uint32_t)v; break;
+    default: static_cast<unsigned long long *>(base)[pos] = v; break;
+  }
+}
+
 // Writes this warp's share of a unit's qualifying rows: for every tile of the
-// unit in order, for the warp's groups, ids in ascending order and then each
-// projected column, at consecutive output slots after the unit's prefix.
-// Masks and group counts come from the scratch the evaluation wrote (L2);
-// projected values are re-read from the columns (the unit was streamed
-// through L2 moments ago).
-__device__ void write_unit(const UnitInfo *U, int cw, int lane) {
+// unit, for the warp's groups (the same groups it evaluated), ids in
+// ascending order and each projected column at consecutive output slots.
+// Pass p of a group covers its rows 32p .. 32p+31 (lane = row); bal[p] is
+// the pass's ballot of qualifying rows.  Projected values are re-read from
+// the columns (the unit streamed through L2 moments ago); all loads of a
+// chunk of up to 2 columns are issued before any store.
+__device__ void write_unit(const UnitInfo *U, const UnitBuf *B, int cw, int lane) {
   const uint64_t cap = U->capacity;
   const int np = U->nproj;
   const uint32_t lt = lanemask_lt();
-  unsigned long long running = U->excl;
-  for (uint32_t tile = U->tile0; tile < U->tile1; ++tile) {
-    const uint32_t r0 = tile * U->tile_rows;
+  const uint32_t ntu = U->tile1 - U->tile0;
+  for (uint32_t ti = 0; ti < ntu; ++ti) {
+    const uint32_t r0 = (U->tile0 + ti) * U->tile_rows;
     const uint32_t rows = min(U->tile_rows, U->nrows - r0);
     const int ngroups = (int)((rows + kGroup - 1) / kGroup);
-    const uint32_t *gc = U->gcounts + (size_t)tile * U->gmax;
-    // exclusive scan of the tile's group counts (<= 128: 4 per lane), same in every warp
-    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    const int gl = lane * 4;
-    if (gl < ngroups) c0 = __ldcg(gc + gl);
-    if (gl + 1 < ngroups) c1 = __ldcg(gc + gl + 1);
-    if (gl + 2 < ngroups) c2 = __ldcg(gc + gl + 2);
-    if (gl + 3 < ngroups) c3 = __ldcg(gc + gl + 3);
-    const uint32_t sum = c0 + c1 + c2 + c3;
-    uint32_t inc = sum;
+    for (int g = cw; g < ngroups; g += kConsumers) {
+      const int idx = (int)ti * (int)U->gmax + g;
+      if (B->gcnt[idx] == 0) continue;
+      const unsigned long long base = U->excl + B->gofs[idx];
+      if (base >= cap) continue;
+      const uint32_t m_even = B->masks[idx * 32 + (lane >> 1)];
+      const uint32_t m_odd = B->masks[idx * 32 + 16 + (lane >> 1)];
+      uint32_t bal[8];
+      uint32_t pos[8];     // output slot of this lane's row in pass p, relative to base
+      uint32_t selbits = 0;
+      uint32_t run = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += y;
-    }
-    const uint32_t e0 = inc - sum, e1 = e0 + c0, e2 = e1 + c1, e3 = e2 + c2;
-    const uint32_t tile_total = __shfl_sync(FULL, inc, 31);
-    if (tile_total != 0 && running < cap) {
-      for (int g = cw; g < ngroups; g += kConsumers) {
-        const int sub = g & 3;
-        const uint32_t cnt = __shfl_sync(FULL, sub == 0 ? c0 : sub == 1 ? c1 : sub == 2 ? c2 : c3, g >> 2);
-        if (cnt == 0) continue;
-        const uint32_t off = __shfl_sync(FULL, sub == 0 ? e0 : sub == 1 ? e1 : sub == 2 ? e2 : e3, g >> 2);
-        const unsigned long long base = running + off;
-        if (base >= cap) continue;
-        const uint8_t *mk = U->masks + ((size_t)tile * U->gmax + g) * 32;
-        const uint32_t m_even = __ldcg(mk + (lane >> 1));
-        const uint32_t m_odd = __ldcg(mk + 16 + (lane >> 1));
-        uint32_t bal[8];
-        uint32_t selbits = 0;
+      for (int p = 0; p < 8; ++p) {
+        const uint32_t sel = (((p & 1) ? m_odd : m_even) >> (2 * (p >> 1) + (lane & 1))) & 1u;
+        bal[p] = __ballot_sync(FULL, sel);
+        selbits |= sel << p;
+        pos[p] = run + __popc(bal[p] & lt);
+        run += __popc(bal[p]);
+      }
+      // rows at or beyond capacity are dropped
+      const uint64_t room = cap - base;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const uint32_t sel = (((p & 1) ? m_odd : m_even) >> (2 * (p >> 1) + (lane & 1))) & 1u;
-          bal[p] = __ballot_sync(FULL, sel);
-          selbits |= sel << p;
-        }
-        const uint32_t row0 = r0 + (uint32_t)g * kGroup + (uint32_t)lane;  // table row of pass 0
-        {
-          unsigned long long run = base;
+      for (int p = 0; p < 8; ++p)
+        if (pos[p] >= room) selbits &= ~(1u << p);
+      const uint32_t row0 = r0 + (uint32_t)g * kGroup + (uint32_t)lane;  // table row of pass 0
 #pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            if ((selbits >> p) & 1u) {
-              const unsigned long long pos = run + __popc(bal[p] & lt);
-              if (pos < cap) U->out_ids[pos] = row0 + 32u * p;
-            }
-            run += __popc(bal[p]);
+      for (int p = 0; p < 8; ++p)
+        if ((selbits >> p) & 1u) U->out_ids[base + pos[p]] = row0 + 32u * p;
+      for (int c0 = 0; c0 < np; c0 += 2) {
+        uint64_t v[2][8];
+        const int nc = min(2, np - c0);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (c < nc) {
+            const int w = U->proj_w[c0 + c];
+            const uint8_t *src = U->proj_ptr[c0 + c];
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+              if ((selbits >> p) & 1u) v[c][p] = load_elem(src, row0 + 32u * p, w);
           }
         }
-        for (int c = 0; c < np; ++c) {
-          const int w = U->proj_w[c];
-          const uint8_t *src = U->proj_ptr[c];
-          void *dst = U->out_proj[c];
-          switch (w) {
-            case 1: sweep_column(src, static_cast<uint8_t *>(dst), base, cap, bal, selbits, lt, row0); break;
-            case 2:
-              sweep_column(reinterpret_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), base, cap, bal,
-                           selbits, lt, row0);
-              break;
-            case 4:
-              sweep_column(reinterpret_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), base, cap, bal,
-                           selbits, lt, row0);
-              break;
-            default:
-              sweep_column(reinterpret_cast<const unsigned long long *>(src),
-                           static_cast<unsigned long long *>(dst), base, cap, bal, selbits, lt, row0);
-              break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (c < nc) {
+            const int w = U->proj_w[c0 + c];
+            void *dst = U->out_proj[c0 + c];
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+              if ((selbits >> p) & 1u) store_elem(dst, base + pos[p], v[c][p], w);
           }
         }
       }
     }
-    running += tile_total;
     retire_tile(U->tiles_left, U->done_ns, lane);
   }
 }
@@ -557,11 +549,11 @@ __device__ void write_unit(const UnitInfo *U, int cw, int lane) {
 struct SmemLayout {
   static constexpr size_t stages = 0;
   static constexpr size_t qslot = stages + (size_t)kStages * kStageBytes;
-  static constexpr size_t uinfo = qslot + (size_t)kStages * sizeof(Query);          // [2] UnitInfo
-  static constexpr size_t utotal = uinfo + 2 * ((sizeof(UnitInfo) + 15) & ~(size_t)15);  // [2] u64
-  static constexpr size_t bars = utotal + 16;           // full[S] empty[S] uevald[2] uready[2]
+  static constexpr size_t ubuf = qslot + (size_t)kStages * sizeof(Query);            // [2] UnitBuf
+  static constexpr size_t uinfo = ubuf + 2 * sizeof(UnitBuf);                          // [2] UnitInfo
+  static constexpr size_t bars = uinfo + 2 * ((sizeof(UnitInfo) + 15) & ~(size_t)15);  // full[S] empty[S] uevald[2] uready[2]
   static constexpr size_t meta = bars + (2 * kStages + 4) * 8;
-  static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);                // [S] int32
+  static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);                  // [S] int32
   static constexpr size_t total = slotq + kStages * 4;
 };
 
@@ -573,8 +565,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *stages = smem + SmemLayout::stages;
   Query *qslot = reinterpret_cast<Query *>(smem + SmemLayout::qslot);
+  UnitBuf *ubuf = reinterpret_cast<UnitBuf *>(smem + SmemLayout::ubuf);
   UnitInfo *uinfo = reinterpret_cast<UnitInfo *>(smem + SmemLayout::uinfo);
-  unsigned long long *utotal = reinterpret_cast<unsigned long long *>(smem + SmemLayout::utotal);
   uint64_t *full_bar = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
   uint64_t *empty_bar = full_bar + kStages;
   uint64_t *uevald_bar = empty_bar + kStages;
@@ -595,7 +587,6 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
     for (int b = 0; b < 2; ++b) {
       mbar_init(&uevald_bar[b], kConsumers);
       mbar_init(&uready_bar[b], 1);
-      utotal[b] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -608,10 +599,14 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
     int qc = 0;  // cursor over queries: tickets of one CTA only increase
     bool done = false;
     while (!done) {
-      uint32_t u = 0;
-      if (lane == 0) u = atomicAdd(&hdr->ticket, 1u);
+      uint32_t u = 0, dead = 0;
+      if (lane == 0) {
+        u = atomicAdd(&hdr->ticket, 1u);
+        dead = aborted(hdr) ? 1u : 0u;
+      }
       u = __shfl_sync(FULL, u, 0);
-      if (u >= L.total_units || aborted(hdr)) {
+      dead = __shfl_sync(FULL, dead, 0);
+      if (u >= L.total_units || dead) {
         if (mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true) && lane == 0) {
           meta[s].q = -1;
           mbar_arrive(&full_bar[s]);
@@ -671,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           m.q = qc;
           m.tile = tile;
           m.rows = rows;
-          m.dead = aborted(hdr) ? 1u : 0u;
+          m.dead = dead;
           m.unit = unit;
           m.useq = useq;
           m.first = tile == t0;
@@ -705,23 +700,24 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       // released; publish it only after every consumer has evaluated this
       // unit, i.e. has finished writing the unit that last used buffer b.
       unsigned long long *status = nullptr, *count = nullptr;
-      UnitInfo r;  // lane 0: scalars; lane c < nproj: column c
+      uint64_t capacity = 0;
+      uint32_t *out_ids = nullptr;
+      unsigned int *tiles_left = nullptr;
+      unsigned long long *done_ns = nullptr;
+      uint32_t tile0 = 0, tile_rows = 0, nrows = 0, gmax = 0;
+      int nproj = 0;
       uint8_t pw = 0;
       const uint8_t *pp = nullptr;
       void *po = nullptr;
-      int nproj = 0;
       if (unit_end) {
-        r.capacity = Q->capacity;
-        r.out_ids = Q->out_ids;
-        r.masks = Q->masks;
-        r.gcounts = Q->gcounts;
-        r.tiles_left = Q->tiles_left;
-        r.done_ns = Q->done_ns;
-        r.tile0 = mt.unit * Q->unit_tiles;
-        r.tile1 = mt.tile + 1;
-        r.tile_rows = Q->tile_rows;
-        r.nrows = Q->nrows;
-        r.gmax = Q->gmax;
+        capacity = Q->capacity;
+        out_ids = Q->out_ids;
+        tiles_left = Q->tiles_left;
+        done_ns = Q->done_ns;
+        tile0 = mt.unit * Q->unit_tiles;
+        tile_rows = Q->tile_rows;
+        nrows = Q->nrows;
+        gmax = Q->gmax;
         nproj = Q->nproj;
         if (lane < nproj) {
           pw = Q->proj_w[lane];
@@ -736,7 +732,30 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       if (unit_end) {
         mbar_wait(&uevald_bar[b], (evp >> b) & 1u, hdr, 2 * kWaitLimitNs, true);
         evp ^= 1u << b;
-        const unsigned long long total = utotal[b];
+        // exclusive scan of the unit's group counts (<= 256: 8 per lane)
+        UnitBuf *B = &ubuf[b];
+        const int ng = (int)((mt.tile + 1 - tile0) * gmax);
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int g = lane * 8 + i;
+          loc[i] = g < ng ? B->gcnt[g] : 0u;
+          sum += loc[i];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int g = lane * 8 + i;
+          if (g < ng) B->gofs[g] = run;
+          run += loc[i];
+        }
+        const unsigned long long total = __shfl_sync(FULL, inc, 31);
         const unsigned long long excl = mt.dead ? 0ull : lookback(status, mt.unit, total, lane, hdr);
         UnitInfo *U = &uinfo[b];
         if (lane < nproj) {
@@ -745,22 +764,17 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           U->out_proj[lane] = po;
         }
         if (lane == 0) {
-          r.excl = excl;
-          r.nproj = nproj;
-          U->excl = r.excl;
-          U->capacity = r.capacity;
-          U->out_ids = r.out_ids;
-          U->masks = r.masks;
-          U->gcounts = r.gcounts;
-          U->tiles_left = r.tiles_left;
-          U->done_ns = r.done_ns;
-          U->tile0 = r.tile0;
-          U->tile1 = r.tile1;
-          U->tile_rows = r.tile_rows;
-          U->nrows = r.nrows;
-          U->gmax = r.gmax;
-          U->nproj = r.nproj;
-          utotal[b] = 0;
+          U->excl = excl;
+          U->capacity = capacity;
+          U->out_ids = out_ids;
+          U->tiles_left = tiles_left;
+          U->done_ns = done_ns;
+          U->tile0 = tile0;
+          U->tile1 = mt.tile + 1;
+          U->tile_rows = tile_rows;
+          U->nrows = nrows;
+          U->gmax = gmax;
+          U->nproj = nproj;
           if (total) atomicAdd(count, total);
         }
         __syncwarp();
@@ -824,32 +838,28 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       retire_tile(Q->tiles_left, Q->done_ns, lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty_bar[s]);
-    } else {  // MODE_COMPACT: evaluate into the mask scratch; the unit is written later
+    } else {  // MODE_COMPACT: evaluate into the unit buffer; the unit is written later
       const uint32_t b = mt.useq & 1u;
       // Buffer b may still be held by an older pending unit: write pending
       // units out, oldest first, until none of them uses b.
       while (mt.first && npend > 0 && (npend == 2 || pend_head == b)) {
         const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
         rdp ^= 1u << pend_head;
-        if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+        if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
         pend_head ^= 1u;
         --npend;
       }
-      uint32_t cnt = 0;
-      uint8_t *mk = Q->masks + (size_t)mt.tile * Q->gmax * 32;
-      uint32_t *gc = Q->gcounts + (size_t)mt.tile * Q->gmax;
-      for (int g = cw; g < ngroups; g += kConsumers) {
-        const uint32_t m = dead ? 0u : (eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
-        mk[g * 32 + lane] = (uint8_t)m;
+      UnitBuf *B = &ubuf[b];
+      const int gbase = (int)((mt.tile - mt.unit * Q->unit_tiles) * Q->gmax);
+      for (int g = cw; g < (int)Q->gmax; g += kConsumers) {
+        const uint32_t m = (dead || g >= ngroups) ? 0u : (eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
+        B->masks[(gbase + g) * 32 + lane] = (uint8_t)m;
         const uint32_t c = (uint32_t)warp_sum(__popc(m));
-        if (lane == 0) gc[g] = c;
-        cnt += c;
+        if (lane == 0) B->gcnt[gbase + g] = c;
       }
-      if (lane == 0 && cnt) atomicAdd(&utotal[b], (unsigned long long)cnt);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty_bar[s]);
       if (mt.last) {
-        __threadfence_block();
         if (lane == 0) mbar_arrive(&uevald_bar[b]);
         if (npend == 0) pend_head = b;
         ++npend;
@@ -858,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
     // write out the oldest evaluated unit once its prefix is known
     if (npend > 0 && mbar_test(&uready_bar[pend_head], (rdp >> pend_head) & 1u)) {
       rdp ^= 1u << pend_head;
-      if (!aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+      if (!aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
       pend_head ^= 1u;
       --npend;
     }
@@ -870,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   while (npend > 0) {  // drain
     const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
     rdp ^= 1u << pend_head;
-    if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], cw, lane);
+    if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
     pend_head ^= 1u;
     --npend;
   }
@@ -969,16 +979,13 @@ void layout_stage(Query &q, int sms) {
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;
   q.gmax = q.tile_rows / kGroup;
   const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);
-  const uint32_t max_ut = (uint32_t)std::max<uint64_t>(1, (512ull * 1024) / tile_bytes);
+  const uint32_t max_ut = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>((512ull * 1024) / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
   const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * 8);
   q.unit_tiles = std::min(std::max<uint32_t>(want, 1), max_ut);
   q.nunits = (q.ntiles + q.unit_tiles - 1) / q.unit_tiles;
 }
 
-// Bytes of device scratch a compaction query needs after its look-back words.
-size_t compact_scratch_bytes(const Query &q) {
-  return (size_t)q.ntiles * q.gmax * 32 + (size_t)q.ntiles * q.gmax * 4;
-}
 
 esc_status alloc_async(void **p, size_t bytes, cudaStream_t st) {
   DeviceState *d;
@@ -1050,11 +1057,10 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.q0.bitmap = bitmap;
   L.nq = 1;
   L.total_units = L.q0.nunits;
-  // scratch: header + count, then (compaction) look-back words (zeroed), masks, group counts
+  // scratch: header + count, then (compaction) one look-back word per unit; all zeroed
   const size_t head = (sizeof(SingleScratch) + 255) & ~(size_t)255;
   const size_t status_bytes = mode == MODE_COMPACT ? (((size_t)L.q0.nunits * 8 + 255) & ~(size_t)255) : 0;
-  const size_t extra = mode == MODE_COMPACT ? compact_scratch_bytes(L.q0) : 0;
-  const size_t bytes = head + status_bytes + extra;
+  const size_t bytes = head + status_bytes;
   void *mem = nullptr;
   if ((s = alloc_async(&mem, bytes, st)) != ESC_OK) return s;
   cudaError_t e = cudaMemsetAsync(mem, 0, head + status_bytes, st);
@@ -1067,11 +1073,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   SingleScratch *sc = static_cast<SingleScratch *>(mem);
   L.hdr = &sc->hdr;
   L.q0.count = dev_count ? dev_count : &sc->count;
-  if (mode == MODE_COMPACT) {
-    L.q0.unit_status = reinterpret_cast<unsigned long long *>(base + head);
-    L.q0.masks = base + head + status_bytes;
-    L.q0.gcounts = reinterpret_cast<uint32_t *>(base + head + status_bytes + (size_t)L.q0.ntiles * L.q0.gmax * 32);
-  }
+  if (mode == MODE_COMPACT) L.q0.unit_status = reinterpret_cast<unsigned long long *>(base + head);
   s = launch_scan(L, st);
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
@@ -1188,7 +1190,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
-  uint64_t units = 0, status_words = 0, extra_bytes = 0;
+  uint64_t units = 0, status_words = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
@@ -1197,10 +1199,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       return s;
     qs[i].unit_base = (uint32_t)units;
     units += qs[i].nunits;
-    if (compact) {
-      status_words += qs[i].nunits;
-      extra_bytes += (compact_scratch_bytes(qs[i]) + 255) & ~(uint64_t)255;
-    }
+    if (compact) status_words += qs[i].nunits;
     if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
   }
   esc_batch *b = new (std::nothrow) esc_batch;
@@ -1214,8 +1213,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
   b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + status_words * 8;  // zeroed every run
   const size_t q_span = (q_bytes + 255) & ~(size_t)255;
-  const size_t work_span = (size_t)extra_bytes;                                   // masks, group counts
-  const size_t total = q_span + b->scratch_bytes + left_bytes + 256 + work_span;
+  const size_t total = q_span + b->scratch_bytes + left_bytes;
   cudaError_t e = cudaMalloc(&b->dev_mem, total);
   if (e != cudaSuccess) {
     batch_free(b);
@@ -1235,7 +1233,6 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   }
   std::vector<unsigned int> init((size_t)n);
   uint64_t so = 0;
-  uint8_t *work = reinterpret_cast<uint8_t *>(((uintptr_t)b->tiles_init + left_bytes + 255) & ~(uintptr_t)255);
   for (int i = 0; i < n; ++i) {
     qs[i].count = &b->counts[i];
     qs[i].done_ns = &b->done[i];
@@ -1243,16 +1240,10 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     if (qs[i].mode == MODE_COMPACT) {
       qs[i].unit_status = status + so;
       so += qs[i].nunits;
-      qs[i].masks = work;
-      qs[i].gcounts = reinterpret_cast<uint32_t *>(work + (size_t)qs[i].ntiles * qs[i].gmax * 32);
-      work += (compact_scratch_bytes(qs[i]) + 255) & ~(size_t)255;
     }
     init[i] = qs[i].ntiles * (unsigned)kConsumers;
   }
-  if ((uintptr_t)work > (uintptr_t)base + total) {
-    batch_free(b);
-    return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
-  }
+
   e = cudaMemcpy(b->queries, qs.data(), q_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->tiles_init, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
