@@ -61,7 +61,11 @@ struct Instr {
 };
 static_assert(sizeof(Instr) == 32, "Instr layout");
 
-enum Mode : int32_t { MODE_COUNT = 0, MODE_COMPACT = 1, MODE_BITMAP = 2 };
+// MODE_COUNT: exact count.  MODE_BITMAP: count + caller's dense-key bitmap.
+// MODE_SELECT: first pass of ordered compaction: count + selection bitmap,
+// per-group counts and per-unit totals in scratch; the write kernel then
+// materialises the rows.
+enum Mode : int32_t { MODE_COUNT = 0, MODE_SELECT = 1, MODE_BITMAP = 2 };
 
 // One sub-query as the scan kernel sees it.  Built on the host per call (or
 // per prepared batch); read-only on the device.
@@ -77,7 +81,7 @@ struct Query {
   uint32_t nunits;
   uint32_t unit_base;     // first global ticket of this query
   uint32_t gmax;          // groups per full tile (tile_rows / kGroup)
-  uint32_t pad0;
+  uint32_t wunit_base;    // first block of this query in the write kernel (compaction only)
   uint32_t stage_off[kMaxRef];    // byte offset of each read column in a stage
   uint8_t ref_w[kMaxRef];         // element width of each read column
   uint8_t proj_w[kMaxProj];
@@ -87,11 +91,13 @@ struct Query {
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];
   uint32_t *out_ids;
-  uint32_t *bitmap;
+  uint32_t *bitmap;               // MODE_BITMAP: caller's bitmap; MODE_SELECT: selection bitmap scratch
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
-  unsigned long long *unit_status;// decoupled look-back words, one per unit (zeroed)
-  unsigned int *tiles_left;       // consumer-warp tile visits left (ntiles x warps, set before launch)
+  uint32_t *gcounts;              // MODE_SELECT: qualifying rows per 256-row group (scratch)
+  unsigned long long *unit_total; // MODE_SELECT: qualifying rows per unit (zeroed)
+  unsigned long long *unit_status;// write kernel's decoupled look-back words, one per unit (zeroed)
+  unsigned int *tiles_left;       // completion countdown (set before launch; see the kernels)
   unsigned long long *done_ns;    // %globaltimer when the last tile finished (may be null)
   Instr code[kMaxInstr];
   int64_t pool[kMaxPool];

@@ -36,14 +36,15 @@
 
 namespace esc {
 
-constexpr int kConsumers = 14;                   // consumer warps per CTA (16 warps in all: 4 per SM sub-partition)
-constexpr int kThreads = 32 * (kConsumers + 2);  // + producer warp + look-back warp
-constexpr int kStages = 4;
-constexpr uint32_t kStageBytes = 44 * 1024;
-constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256
+constexpr int kConsumers = 15;                   // consumer warps per CTA
+constexpr int kThreads = 32 * (kConsumers + 1);  // + the producer warp: 16 warps, 4 per SM sub-partition
+constexpr int kStages = 3;
+constexpr uint32_t kStageBytes = 64 * 1024;
+constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256: one write-kernel thread per group
+constexpr int kWriteThreads = kMaxUnitGroups;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr uint32_t FULL = 0xffffffffu;
-static_assert(kStageBytes <= 65536, "stage offsets are 16-bit");
+static_assert(kStageBytes <= 65536, "stage column offsets are 16-bit");
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -247,10 +248,15 @@ __device__ __forceinline__ int64_t udf_rem(int64_t a, int64_t b, uint64_t d, uin
 }
 
 // ------------------------------------------------------------------ evaluation
-// Runs the program on this lane's 8 rows of group `grp` of the staged tile.
+// Runs the program on this lane's 8 rows of NG groups of the staged tile at
+// once (one decode per instruction for all of them, NG independent chains).
 // Q (program included) lives in shared memory.
-__device__ __forceinline__ uint32_t eval_group(const Query *Q, const uint8_t *stage, int grp, int lane) {
-  uint64_t S = 0;  // evaluation stack: entry k in bits [8k, 8k+8), top at bits 0..7
+template <int NG>
+__device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage, const int (&grp)[NG], int lane,
+                                            uint32_t (&out)[NG]) {
+  uint64_t S[NG];  // evaluation stacks: entry k in bits [8k, 8k+8), top at bits 0..7
+#pragma unroll
+  for (int i = 0; i < NG; ++i) S[i] = 0;
   const int n = Q->ninstr;
   for (int pc = 0; pc < n; ++pc) {
     const uint4 h = *reinterpret_cast<const uint4 *>(&Q->code[pc]);
@@ -258,76 +264,99 @@ __device__ __forceinline__ uint32_t eval_group(const Query *Q, const uint8_t *st
     if (op <= OP_UDF) {
       const longlong2 lh = *reinterpret_cast<const longlong2 *>(&Q->code[pc].lo);
       const int dt = (int)((h.x >> 8) & 0xffu);
-      const uint32_t soff = h.z >> 16;
-      const uint8_t *g = stage + soff + (size_t)grp * kGroup * width_of(dt);
-      uint32_t m = 0;
+      const int w = width_of(dt);
+      const uint8_t *col = stage + (h.z >> 16);
+      uint32_t m[NG];
+#pragma unroll
+      for (int i = 0; i < NG; ++i) m[i] = 0;
       if (op == OP_RANGE) {
         if (dt == ESC_I64) {
-          int64_t v[8];
-          load8(dt, g, lane, v);
+          int64_t v[NG][8];
+#pragma unroll
+          for (int i = 0; i < NG; ++i) load8(dt, col + (size_t)grp[i] * kGroup * 8, lane, v[i]);
           const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint64_t)v[k] - (uint64_t)lh.x <= span) << k;
+          for (int i = 0; i < NG; ++i)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)((uint64_t)v[i][k] - (uint64_t)lh.x <= span) << k;
         } else {
-          int32_t v[8];
-          load8_32(dt, g, lane, v);
+          int32_t v[NG][8];
+#pragma unroll
+          for (int i = 0; i < NG; ++i) load8_32(dt, col + (size_t)grp[i] * kGroup * w, lane, v[i]);
           const uint32_t lo = (uint32_t)lh.x;
           const uint32_t span = (uint32_t)((uint64_t)lh.y - (uint64_t)lh.x);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) m |= (uint32_t)((uint32_t)v[k] - lo <= span) << k;
+          for (int i = 0; i < NG; ++i)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)((uint32_t)v[i][k] - lo <= span) << k;
         }
       } else if (op == OP_IN) {
         const int64_t *vals = &Q->pool[h.z & 0xffffu];
         const int nv = (int)(h.y >> 16);
         if (dt == ESC_I64) {
-          int64_t v[8];
-          load8(dt, g, lane, v);
+          int64_t v[NG][8];
+#pragma unroll
+          for (int i = 0; i < NG; ++i) load8(dt, col + (size_t)grp[i] * kGroup * 8, lane, v[i]);
           for (int t = 0; t < nv; ++t) {
             const int64_t c = vals[t];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+              for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)(v[i][k] == c) << k;
           }
         } else {
-          int32_t v[8];
-          load8_32(dt, g, lane, v);
+          int32_t v[NG][8];
+#pragma unroll
+          for (int i = 0; i < NG; ++i) load8_32(dt, col + (size_t)grp[i] * kGroup * w, lane, v[i]);
           for (int t = 0; t < nv; ++t) {
             const int32_t c = (int32_t)vals[t];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) m |= (uint32_t)(v[k] == c) << k;
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+              for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)(v[i][k] == c) << k;
           }
         }
       } else {  // OP_UDF
         const int dt2 = (int)((h.x >> 16) & 0xffu);
-        const uint32_t soff2 = h.w & 0xffffu;
-        int64_t a[8], b[8];
-        load8(dt, g, lane, a);
-        load8(dt2, stage + soff2 + (size_t)grp * kGroup * width_of(dt2), lane, b);
+        const int w2 = width_of(dt2);
+        const uint8_t *col2 = stage + (h.w & 0xffffu);
         const int64_t *P = &Q->pool[h.z & 0xffffu];
         const uint64_t d = (uint64_t)P[0], mult = (uint64_t)P[1];
         const int sh1 = (int)P[2], sh2 = (int)P[3];
         const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
-          m |= (uint32_t)((uint64_t)r - (uint64_t)lh.x <= span) << k;
+        for (int i = 0; i < NG; ++i) {
+          int64_t a[8], b[8];
+          load8(dt, col + (size_t)grp[i] * kGroup * w, lane, a);
+          load8(dt2, col2 + (size_t)grp[i] * kGroup * w2, lane, b);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
+            m[i] |= (uint32_t)((uint64_t)r - (uint64_t)lh.x <= span) << k;
+          }
         }
       }
-      S = (S << 8) | m;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = (S[i] << 8) | m[i];
     } else if (op == OP_AND) {
-      const uint64_t top = S & 0xffu;
-      S = (S >> 8) & (top | ~0xffull);
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = (S[i] >> 8) & ((S[i] & 0xffu) | ~0xffull);
     } else if (op == OP_OR) {
-      const uint64_t top = S & 0xffu;
-      S = (S >> 8) | top;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = (S[i] >> 8) | (S[i] & 0xffu);
     } else if (op == OP_NOT) {
-      S ^= 0xffu;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] ^= 0xffu;
     } else if (op == OP_TRUE) {
-      S = (S << 8) | 0xffu;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = (S[i] << 8) | 0xffu;
     } else {  // OP_FALSE
-      S = S << 8;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = S[i] << 8;
     }
   }
-  return (uint32_t)(S & 0xffu);
+#pragma unroll
+  for (int i = 0; i < NG; ++i) out[i] = (uint32_t)(S[i] & 0xffu);
 }
 
 // Bits of this lane's 8 rows that lie inside the tile's `rows` valid rows.
@@ -346,72 +375,19 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
-// Exclusive prefix of this tile among all earlier tiles of the same query,
-// by decoupled look-back (one warp).  Publishes the tile's aggregate first,
-// then its inclusive prefix.  Word = flag (bits 62..63: 1 aggregate,
-// 2 inclusive prefix) | value (bits 0..61).
-__device__ unsigned long long lookback(unsigned long long *st, uint32_t tile, unsigned long long total, int lane,
-                                       ScratchHdr *hdr) {
-  const unsigned long long FA = 1ull << 62, FP = 2ull << 62, VM = FA - 1;
-  if (tile == 0) {
-    if (lane == 0) st_relaxed(&st[0], FP | total);
-    return 0;
-  }
-  if (lane == 0) st_relaxed(&st[tile], FA | total);
-  unsigned long long excl = 0;
-  long long idx = (long long)tile - 1;
-  const uint64_t t0 = globaltimer();
-  uint32_t polls = 0;
-  bool ok = true;
-  while (true) {
-    const long long j = idx - lane;
-    unsigned long long w = j >= 0 ? ld_relaxed(&st[j]) : FP;
-    while (__any_sync(FULL, (w >> 62) == 0)) {
-      if ((w >> 62) == 0) {
-        __nanosleep(20);
-        w = ld_relaxed(&st[j]);
-      }
-      if ((++polls & 31u) == 0) {
-        const bool late = __shfl_sync(FULL, (int)(globaltimer() - t0 > kWaitLimitNs), 0) != 0;
-        if (late || aborted(hdr)) {
-          ok = false;
-          break;
-        }
-      }
-    }
-    if (!ok) break;
-    const uint32_t pm = __ballot_sync(FULL, (w >> 62) == 2);
-    if (pm) {
-      const int first = __ffs(pm) - 1;
-      excl += warp_sum(lane <= first ? (w & VM) : 0ull);
-      break;
-    }
-    excl += warp_sum(w & VM);
-    idx -= 32;
-  }
-  if (!ok) {
-    if (lane == 0) raise_status(hdr, ESC_ETIMEOUT);
-    return 0;
-  }
-  if (lane == 0) st_relaxed(&st[tile], FP | (excl + total));
-  return excl;
-}
-
 struct StageMeta {
   int32_t q;       // query index, -1 = end of work
   uint32_t tile;   // tile index within the query
   uint32_t rows;   // valid rows in this tile
   uint32_t dead;   // 1: the launch is aborting, skip the work (same for every reader)
   uint32_t unit;   // unit index within the query
-  uint32_t useq;   // this CTA's running unit number (selects the unit buffer)
-  uint32_t first;  // first tile of its unit
-  uint32_t last;   // last tile of its unit
+  uint32_t pad[3];
 };
 
 struct Launch {
   const Query *queries;  // device array of nq queries, or null: use q0
   int32_t nq;
-  uint32_t total_units;
+  uint32_t total_units;  // scan kernel: work units; write kernel: blocks
   ScratchHdr *hdr;
   uint32_t pad[4];
   Query q0;
@@ -421,31 +397,6 @@ __device__ __forceinline__ const Query *query_ptr(const Launch &L, int q) {
   return L.queries ? &L.queries[q] : &L.q0;
 }
 
-// What the write-out of one compaction unit needs, copied out of the staged
-// query by the look-back warp (the stage may be reused before the write).
-struct UnitInfo {
-  unsigned long long excl;       // exclusive prefix of the unit's first row
-  uint64_t capacity;
-  uint32_t *out_ids;
-  unsigned int *tiles_left;
-  unsigned long long *done_ns;
-  uint32_t tile0, tile1;         // the unit's tiles [tile0, tile1)
-  uint32_t tile_rows, nrows, gmax;
-  int32_t nproj;
-  uint8_t proj_w[kMaxProj];
-  const uint8_t *proj_ptr[kMaxProj];
-  void *out_proj[kMaxProj];
-};
-
-// Per-unit compaction state in shared memory (two buffers, alternating
-// units): each evaluated group's 8-bit lane masks (32 bytes), its count of
-// qualifying rows, and its exclusive offset within the unit.
-struct UnitBuf {
-  uint8_t masks[kMaxUnitGroups * 32];
-  uint32_t gcnt[kMaxUnitGroups];
-  uint32_t gofs[kMaxUnitGroups];
-};
-
 __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned long long *done_ns, int lane) {
   // Per-query completion time: every consumer warp retires each tile once.
   if (done_ns && lane == 0) {
@@ -454,123 +405,25 @@ __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned l
   }
 }
 
-__device__ __forceinline__ uint64_t load_elem(const uint8_t *base, uint32_t row, int w) {
-  switch (w) {
-    case 1: return base[row];
-    case 2: return reinterpret_cast<const uint16_t *>(base)[row];
-    case 4: return reinterpret_cast<const uint32_t *>(base)[row];
-    default: return reinterpret_cast<const unsigned long long *>(base)[row];
-  }
-}
-
-__device__ __forceinline__ void store_elem(void *base, unsigned long long pos, uint64_t v, int w) {
-  switch (w) {
-    case 1: static_cast<uint8_t *>(base)[pos] = (uint8_t)v; break;
-    case 2: static_cast<uint16_t *>(base)[pos] = (uint16_t)v; break;
-    case 4: static_cast<uint32_t *>(base)[pos] = (uint32_t)v; break;
-    default: static_cast<unsigned long long *>(base)[pos] = v; break;
-  }
-}
-
-// Writes this warp's share of a unit's qualifying rows: for every tile of the
-// unit, for the warp's groups (the same groups it evaluated), ids in
-// ascending order and each projected column at consecutive output slots.
-// Pass p of a group covers its rows 32p .. 32p+31 (lane = row); bal[p] is
-// the pass's ballot of qualifying rows.  Projected values are re-read from
-// the columns (the unit streamed through L2 moments ago); all loads of a
-// chunk of up to 2 columns are issued before any store.
-__device__ void write_unit(const UnitInfo *U, const UnitBuf *B, int cw, int lane) {
-  const uint64_t cap = U->capacity;
-  const int np = U->nproj;
-  const uint32_t lt = lanemask_lt();
-  const uint32_t ntu = U->tile1 - U->tile0;
-  for (uint32_t ti = 0; ti < ntu; ++ti) {
-    const uint32_t r0 = (U->tile0 + ti) * U->tile_rows;
-    const uint32_t rows = min(U->tile_rows, U->nrows - r0);
-    const int ngroups = (int)((rows + kGroup - 1) / kGroup);
-    for (int g = cw; g < ngroups; g += kConsumers) {
-      const int idx = (int)ti * (int)U->gmax + g;
-      if (B->gcnt[idx] == 0) continue;
-      const unsigned long long base = U->excl + B->gofs[idx];
-      if (base >= cap) continue;
-      const uint32_t m_even = B->masks[idx * 32 + (lane >> 1)];
-      const uint32_t m_odd = B->masks[idx * 32 + 16 + (lane >> 1)];
-      uint32_t bal[8];
-      uint32_t pos[8];     // output slot of this lane's row in pass p, relative to base
-      uint32_t selbits = 0;
-      uint32_t run = 0;
-#pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const uint32_t sel = (((p & 1) ? m_odd : m_even) >> (2 * (p >> 1) + (lane & 1))) & 1u;
-        bal[p] = __ballot_sync(FULL, sel);
-        selbits |= sel << p;
-        pos[p] = run + __popc(bal[p] & lt);
-        run += __popc(bal[p]);
-      }
-      // rows at or beyond capacity are dropped
-      const uint64_t room = cap - base;
-#pragma unroll
-      for (int p = 0; p < 8; ++p)
-        if (pos[p] >= room) selbits &= ~(1u << p);
-      const uint32_t row0 = r0 + (uint32_t)g * kGroup + (uint32_t)lane;  // table row of pass 0
-#pragma unroll
-      for (int p = 0; p < 8; ++p)
-        if ((selbits >> p) & 1u) U->out_ids[base + pos[p]] = row0 + 32u * p;
-      for (int c0 = 0; c0 < np; c0 += 2) {
-        uint64_t v[2][8];
-        const int nc = min(2, np - c0);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          if (c < nc) {
-            const int w = U->proj_w[c0 + c];
-            const uint8_t *src = U->proj_ptr[c0 + c];
-#pragma unroll
-            for (int p = 0; p < 8; ++p)
-              if ((selbits >> p) & 1u) v[c][p] = load_elem(src, row0 + 32u * p, w);
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          if (c < nc) {
-            const int w = U->proj_w[c0 + c];
-            void *dst = U->out_proj[c0 + c];
-#pragma unroll
-            for (int p = 0; p < 8; ++p)
-              if ((selbits >> p) & 1u) store_elem(dst, base + pos[p], v[c][p], w);
-          }
-        }
-      }
-    }
-    retire_tile(U->tiles_left, U->done_ns, lane);
-  }
-}
-
 // Shared-memory layout of the scan kernel (offsets in bytes).
 struct SmemLayout {
   static constexpr size_t stages = 0;
   static constexpr size_t qslot = stages + (size_t)kStages * kStageBytes;
-  static constexpr size_t ubuf = qslot + (size_t)kStages * sizeof(Query);            // [2] UnitBuf
-  static constexpr size_t uinfo = ubuf + 2 * sizeof(UnitBuf);                          // [2] UnitInfo
-  static constexpr size_t bars = uinfo + 2 * ((sizeof(UnitInfo) + 15) & ~(size_t)15);  // full[S] empty[S] uevald[2] uready[2]
-  static constexpr size_t meta = bars + (2 * kStages + 4) * 8;
-  static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);                  // [S] int32
+  static constexpr size_t bars = qslot + (size_t)kStages * sizeof(Query);  // full[S] empty[S]
+  static constexpr size_t meta = bars + 2 * kStages * 8;
+  static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);      // [S] int32
   static constexpr size_t total = slotq + kStages * 4;
 };
 
-// ------------------------------------------------------------------ the kernel
-// Warp 0: producer (unit tickets, bulk copies).  Warp 1: look-back (unit
-// prefixes for ordered compaction).  Warps 2..: consumers (evaluate, count,
-// write).
+// ------------------------------------------------------------------ the scan kernel
+// Warp 0: producer (unit tickets, bulk copies).  Warps 1..: consumers
+// (evaluate; count; write bitmap words, group counts and unit totals).
 __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *stages = smem + SmemLayout::stages;
   Query *qslot = reinterpret_cast<Query *>(smem + SmemLayout::qslot);
-  UnitBuf *ubuf = reinterpret_cast<UnitBuf *>(smem + SmemLayout::ubuf);
-  UnitInfo *uinfo = reinterpret_cast<UnitInfo *>(smem + SmemLayout::uinfo);
   uint64_t *full_bar = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
   uint64_t *empty_bar = full_bar + kStages;
-  uint64_t *uevald_bar = empty_bar + kStages;
-  uint64_t *uready_bar = uevald_bar + 2;
   StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SmemLayout::meta);
   int32_t *slotq = reinterpret_cast<int32_t *>(smem + SmemLayout::slotq);
 
@@ -581,12 +434,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], kConsumers + 1);
+      mbar_init(&empty_bar[s], kConsumers);
       slotq[s] = -1;
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&uevald_bar[b], kConsumers);
-      mbar_init(&uready_bar[b], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -595,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     int s = 0;
-    uint32_t phase = 0, useq = 0;
+    uint32_t phase = 0;
     int qc = 0;  // cursor over queries: tickets of one CTA only increase
     bool done = false;
     while (!done) {
@@ -659,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           }
           fence_proxy_async_smem();
         }
-        const unsigned long long tot = warp_sum(bulk);
+        const uint32_t tot = __reduce_add_sync(FULL, bulk);
         __syncwarp();
         if (lane == 0) {
           StageMeta &m = meta[s];
@@ -668,10 +517,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           m.rows = rows;
           m.dead = dead;
           m.unit = unit;
-          m.useq = useq;
-          m.first = tile == t0;
-          m.last = tile + 1 == t1;
-          mbar_arrive_expect_tx(&full_bar[s], (uint32_t)tot);
+          mbar_arrive_expect_tx(&full_bar[s], tot);
         }
         __syncwarp();
         if (bulk) bulk_load(dst, src, bulk, &full_bar[s]);
@@ -680,209 +526,320 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           phase ^= 1u;
         }
       }
-      ++useq;
-    }
-    return;
-  }
-
-  if (warp == 1) {
-    // ---------------------------------------------------------------- look-back
-    int s = 0;
-    uint32_t phase = 0, evp = 0;  // evp bit b: parity of uevald_bar[b]
-    while (true) {
-      if (!mbar_wait(&full_bar[s], phase, hdr)) break;
-      const StageMeta mt = meta[s];
-      if (mt.q < 0) break;
-      const Query *Q = &qslot[s];
-      const bool unit_end = Q->mode == MODE_COMPACT && mt.last;
-      const uint32_t b = mt.useq & 1u;
-      // Copy what the write-out needs into registers before the stage is
-      // released; publish it only after every consumer has evaluated this
-      // unit, i.e. has finished writing the unit that last used buffer b.
-      unsigned long long *status = nullptr, *count = nullptr;
-      uint64_t capacity = 0;
-      uint32_t *out_ids = nullptr;
-      unsigned int *tiles_left = nullptr;
-      unsigned long long *done_ns = nullptr;
-      uint32_t tile0 = 0, tile_rows = 0, nrows = 0, gmax = 0;
-      int nproj = 0;
-      uint8_t pw = 0;
-      const uint8_t *pp = nullptr;
-      void *po = nullptr;
-      if (unit_end) {
-        capacity = Q->capacity;
-        out_ids = Q->out_ids;
-        tiles_left = Q->tiles_left;
-        done_ns = Q->done_ns;
-        tile0 = mt.unit * Q->unit_tiles;
-        tile_rows = Q->tile_rows;
-        nrows = Q->nrows;
-        gmax = Q->gmax;
-        nproj = Q->nproj;
-        if (lane < nproj) {
-          pw = Q->proj_w[lane];
-          pp = Q->proj_ptr[lane];
-          po = Q->out_proj[lane];
-        }
-        status = Q->unit_status;
-        count = Q->count;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty_bar[s]);
-      if (unit_end) {
-        mbar_wait(&uevald_bar[b], (evp >> b) & 1u, hdr, 2 * kWaitLimitNs, true);
-        evp ^= 1u << b;
-        // exclusive scan of the unit's group counts (<= 256: 8 per lane)
-        UnitBuf *B = &ubuf[b];
-        const int ng = (int)((mt.tile + 1 - tile0) * gmax);
-        uint32_t loc[8], sum = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int g = lane * 8 + i;
-          loc[i] = g < ng ? B->gcnt[g] : 0u;
-          sum += loc[i];
-        }
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(FULL, inc, o);
-          if (lane >= o) inc += y;
-        }
-        uint32_t run = inc - sum;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int g = lane * 8 + i;
-          if (g < ng) B->gofs[g] = run;
-          run += loc[i];
-        }
-        const unsigned long long total = __shfl_sync(FULL, inc, 31);
-        const unsigned long long excl = mt.dead ? 0ull : lookback(status, mt.unit, total, lane, hdr);
-        UnitInfo *U = &uinfo[b];
-        if (lane < nproj) {
-          U->proj_w[lane] = pw;
-          U->proj_ptr[lane] = pp;
-          U->out_proj[lane] = po;
-        }
-        if (lane == 0) {
-          U->excl = excl;
-          U->capacity = capacity;
-          U->out_ids = out_ids;
-          U->tiles_left = tiles_left;
-          U->done_ns = done_ns;
-          U->tile0 = tile0;
-          U->tile1 = mt.tile + 1;
-          U->tile_rows = tile_rows;
-          U->nrows = nrows;
-          U->gmax = gmax;
-          U->nproj = nproj;
-          if (total) atomicAdd(count, total);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&uready_bar[b]);
-      }
-      if (++s == kStages) {
-        s = 0;
-        phase ^= 1u;
-      }
     }
     return;
   }
 
   // ---------------------------------------------------------------- consumers
-  const int cw = warp - 2;
+  const int cw = warp - 1;
   int s = 0;
-  uint32_t phase = 0, rdp = 0;  // rdp bit b: parity of uready_bar[b]
-  int npend = 0;                // compaction units evaluated but not yet written (<= 2)
-  uint32_t pend_head = 0;       // unit buffer of the oldest pending unit
+  uint32_t phase = 0;
+  // Running sums flushed with one atomic when the query / unit changes.
+  unsigned long long *acc_ptr = nullptr;  // query count being accumulated
+  int acc_q = -1;
+  uint32_t acc = 0;                       // this lane's share
+  unsigned long long *uacc_ptr = nullptr; // unit total being accumulated (MODE_SELECT)
+  uint32_t uacc = 0;
   while (true) {
-    if (!mbar_wait(&full_bar[s], phase, hdr)) break;
+    const bool got = mbar_wait(&full_bar[s], phase, hdr);
     const StageMeta mt = meta[s];
-    if (mt.q < 0) break;
+    const bool end = !got || mt.q < 0;
     const Query *Q = &qslot[s];
+    unsigned long long *uptr = (!end && Q->mode == MODE_SELECT) ? Q->unit_total + mt.unit : nullptr;
+    if (uacc_ptr && (end || uptr != uacc_ptr)) {
+      const uint32_t t = __reduce_add_sync(FULL, uacc);
+      if (lane == 0 && t) atomicAdd(uacc_ptr, (unsigned long long)t);
+      uacc = 0;
+      uacc_ptr = nullptr;
+    }
+    if (acc_ptr && (end || acc_q != mt.q)) {
+      const uint32_t t = __reduce_add_sync(FULL, acc);
+      if (lane == 0 && t) atomicAdd(acc_ptr, (unsigned long long)t);
+      acc = 0;
+      acc_ptr = nullptr;
+      acc_q = -1;
+    }
+    if (end) break;
     const uint8_t *stage = stages + (size_t)s * kStageBytes;
     const uint32_t rows = mt.rows;
     const int ngroups = (int)((rows + kGroup - 1) / kGroup);
     const int mode = Q->mode;
     const uint32_t r0 = mt.tile * Q->tile_rows;
-    const bool dead = mt.dead != 0;
-    if (mode == MODE_COUNT) {
-      uint32_t cnt = 0;
-      if (!dead)
-        for (int g = cw; g < ngroups; g += kConsumers)
-          cnt += __popc(eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
-      const unsigned long long tot = warp_sum(cnt);
-      if (lane == 0 && tot) atomicAdd(Q->count, tot);
-      retire_tile(Q->tiles_left, Q->done_ns, lane);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty_bar[s]);
-    } else if (mode == MODE_BITMAP) {
-      uint32_t cnt = 0;
-      const uint32_t nwords = (Q->nrows + 31u) / 32u;
-      if (!dead)
-        for (int g = cw; g < ngroups; g += kConsumers) {
-          const uint32_t m = eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows);
-          cnt += __popc(m);
-          uint32_t word = 0;
-#pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const int src = 16 * (p & 1) + (lane >> 1);
-            const int bit = 2 * (p >> 1) + (lane & 1);
-            const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
-            if (lane == p) word = bb;
-          }
-          const uint32_t wi = (r0 + (uint32_t)g * kGroup) / 32u + (uint32_t)lane;
-          if (lane < 8 && wi < nwords) Q->bitmap[wi] = word;
+    acc_q = mt.q;
+    acc_ptr = Q->count;
+    uacc_ptr = uptr;
+    if (mt.dead == 0) {
+      if (mode == MODE_COUNT) {
+        for (int g = cw; g < ngroups; g += 2 * kConsumers) {
+          const int g1 = g + kConsumers;
+          const int gs[2] = {g, g1 < ngroups ? g1 : g};
+          uint32_t m[2];
+          eval_groups<2>(Q, stage, gs, lane, m);
+          acc += __popc(m[0] & valid_mask(g, lane, rows));
+          if (g1 < ngroups) acc += __popc(m[1] & valid_mask(g1, lane, rows));
         }
-      const unsigned long long tot = warp_sum(cnt);
-      if (lane == 0 && tot) atomicAdd(Q->count, tot);
-      retire_tile(Q->tiles_left, Q->done_ns, lane);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty_bar[s]);
-    } else {  // MODE_COMPACT: evaluate into the unit buffer; the unit is written later
-      const uint32_t b = mt.useq & 1u;
-      // Buffer b may still be held by an older pending unit: write pending
-      // units out, oldest first, until none of them uses b.
-      while (mt.first && npend > 0 && (npend == 2 || pend_head == b)) {
-        const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
-        rdp ^= 1u << pend_head;
-        if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
-        pend_head ^= 1u;
-        --npend;
-      }
-      UnitBuf *B = &ubuf[b];
-      const int gbase = (int)((mt.tile - mt.unit * Q->unit_tiles) * Q->gmax);
-      for (int g = cw; g < (int)Q->gmax; g += kConsumers) {
-        const uint32_t m = (dead || g >= ngroups) ? 0u : (eval_group(Q, stage, g, lane) & valid_mask(g, lane, rows));
-        B->masks[(gbase + g) * 32 + lane] = (uint8_t)m;
-        const uint32_t c = (uint32_t)warp_sum(__popc(m));
-        if (lane == 0) B->gcnt[gbase + g] = c;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty_bar[s]);
-      if (mt.last) {
-        if (lane == 0) mbar_arrive(&uevald_bar[b]);
-        if (npend == 0) pend_head = b;
-        ++npend;
+      } else {  // MODE_BITMAP / MODE_SELECT: one bitmap word per 32 rows
+        const uint32_t nwords = (Q->nrows + 31u) / 32u;
+        uint32_t *bm = Q->bitmap;
+        uint32_t *gc = mode == MODE_SELECT ? Q->gcounts : nullptr;
+        for (int g = cw; g < ngroups; g += 2 * kConsumers) {
+          const int g1 = g + kConsumers;
+          const int gs[2] = {g, g1 < ngroups ? g1 : g};
+          uint32_t mm[2];
+          eval_groups<2>(Q, stage, gs, lane, mm);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            if (i == 1 && g1 >= ngroups) break;
+            const uint32_t m = mm[i] & valid_mask(gs[i], lane, rows);
+            const uint32_t c = __popc(m);
+            acc += c;
+            uacc += c;
+            uint32_t word = 0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {  // words of rows 32p .. 32p+31 of the group
+              const int src = 16 * (p & 1) + (lane >> 1);
+              const int bit = 2 * (p >> 1) + (lane & 1);
+              const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
+              if (lane == p) word = bb;
+            }
+            const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
+            const uint32_t wi = gidx * 8u + (uint32_t)lane;
+            if (lane < 8 && wi < nwords) bm[wi] = word;
+            if (gc) {
+              const uint32_t gcount = __reduce_add_sync(FULL, c);
+              if (lane == 0) gc[gidx] = gcount;
+            }
+          }
+        }
       }
     }
-    // write out the oldest evaluated unit once its prefix is known
-    if (npend > 0 && mbar_test(&uready_bar[pend_head], (rdp >> pend_head) & 1u)) {
-      rdp ^= 1u << pend_head;
-      if (!aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
-      pend_head ^= 1u;
-      --npend;
-    }
+    if (mode != MODE_SELECT) retire_tile(Q->tiles_left, Q->done_ns, lane);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[s]);
     if (++s == kStages) {
       s = 0;
       phase ^= 1u;
     }
   }
-  while (npend > 0) {  // drain
-    const bool ok = mbar_wait(&uready_bar[pend_head], (rdp >> pend_head) & 1u, hdr, 2 * kWaitLimitNs, true);
-    rdp ^= 1u << pend_head;
-    if (ok && !aborted(hdr)) write_unit(&uinfo[pend_head], &ubuf[pend_head], cw, lane);
-    pend_head ^= 1u;
-    --npend;
+}
+
+// ------------------------------------------------------------------ the write kernel
+// Second pass of ordered compaction: one block per work unit (<= 65536
+// rows, <= 256 groups of 256 rows).  The unit's output offset comes from a
+// decoupled look-back over the units before it (Merrill & Garland 2016):
+// every unit's aggregate is already final (written by the scan kernel), so
+// the look-back adds aggregates until it meets a unit whose inclusive prefix
+// another block has published, and never waits.  Group offsets within the
+// unit come from a block-wide scan of the group counts; each warp then
+// writes its 32 groups' qualifying rows: ids, then every projected column.
+//
+// Writes use a gather queue: each group's qualifying rows are spread
+// densely over the lanes (entry j -> lane j % 32) and pushed as packed
+// (row within unit << 16 | slot within unit) into 8 slots per lane; a flush
+// issues all loads of the queued rows for two columns before any store.
+
+// Position of the r-th set bit (0-based) of x; r < popc(x).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t r) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const uint32_t c = __popc(x & ((1u << w) - 1u));
+    if (r >= c) {
+      r -= c;
+      x >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+__device__ __forceinline__ uint64_t load_elem(const uint8_t *base, uint32_t row, int w) {
+  switch (w) {
+    case 1: return base[row];
+    case 2: return reinterpret_cast<const uint16_t *>(base)[row];
+    case 4: return reinterpret_cast<const uint32_t *>(base)[row];
+    default: return reinterpret_cast<const unsigned long long *>(base)[row];
+  }
+}
+
+__device__ __forceinline__ void store_elem(void *base, unsigned long long pos, uint64_t v, int w) {
+  switch (w) {
+    case 1: static_cast<uint8_t *>(base)[pos] = (uint8_t)v; break;
+    case 2: static_cast<uint16_t *>(base)[pos] = (uint16_t)v; break;
+    case 4: static_cast<uint32_t *>(base)[pos] = (uint32_t)v; break;
+    default: static_cast<unsigned long long *>(base)[pos] = v; break;
+  }
+}
+
+struct WriteCtx {
+  const Query *Q;
+  uint32_t urow0;            // unit's first row
+  unsigned long long excl;   // unit's first output slot
+  uint64_t cap;
+  int np;
+};
+
+__device__ __forceinline__ void flush_queue(const WriteCtx &C, const uint32_t (&q)[8], uint32_t valid) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (((valid >> k) & 1u) && C.excl + (q[k] & 0xffffu) >= C.cap) valid &= ~(1u << k);
+  uint32_t *ids = C.Q->out_ids;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((valid >> k) & 1u) ids[C.excl + (q[k] & 0xffffu)] = C.urow0 + (q[k] >> 16);
+  for (int c0 = 0; c0 < C.np; c0 += 2) {
+    const int nc = min(2, C.np - c0);
+    uint64_t v[2][8];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c < nc) {
+        const int w = C.Q->proj_w[c0 + c];
+        const uint8_t *src = C.Q->proj_ptr[c0 + c];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if ((valid >> k) & 1u) v[c][k] = load_elem(src, C.urow0 + (q[k] >> 16), w);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c < nc) {
+        const int w = C.Q->proj_w[c0 + c];
+        void *dst = C.Q->out_proj[c0 + c];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if ((valid >> k) & 1u) store_elem(dst, C.excl + (q[k] & 0xffffu), v[c][k], w);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_constant__ Launch L) {
+  __shared__ Query sq;                      // this block's query
+  __shared__ uint32_t wsum[kWriteThreads / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ int s_q;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  // which query (batches: the last one whose first write block is <= blockIdx.x)
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = L.nq - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (query_ptr(L, mid)->wunit_base <= blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_q = lo;
+  }
+  __syncthreads();
+  {
+    const uint2 *src = reinterpret_cast<const uint2 *>(query_ptr(L, s_q));
+    uint2 *dst = reinterpret_cast<uint2 *>(&sq);
+    for (int i = threadIdx.x; i < (int)(sizeof(Query) / 8); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const Query *Q = &sq;
+  const uint32_t u = blockIdx.x - Q->wunit_base;
+  const uint32_t urows = Q->unit_tiles * Q->tile_rows;
+  const uint32_t urow0 = u * urows;
+  const uint32_t rows = min(urows, Q->nrows - urow0);
+  const int ng = (int)((rows + kGroup - 1) / kGroup);
+  const uint32_t g0 = urow0 / kGroup;
+  // block-wide exclusive scan of the group counts (one group per thread)
+  const uint32_t c = (int)threadIdx.x < ng ? Q->gcounts[g0 + threadIdx.x] : 0u;
+  uint32_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  // look-back for the unit's exclusive prefix (warp 0)
+  if (warp == 0) {
+    const unsigned long long FP = 2ull << 62, VM = (1ull << 62) - 1;
+    unsigned long long *st = Q->unit_status;
+    const unsigned long long *tot = Q->unit_total;
+    unsigned long long excl = 0;
+    long long idx = (long long)u - 1;
+    while (idx >= 0) {
+      const long long j = idx - lane;
+      unsigned long long w = FP, t = 0;
+      if (j >= 0) {
+        w = ld_relaxed(&st[j]);
+        t = tot[j];
+      }
+      const uint32_t pm = __ballot_sync(FULL, (w >> 62) == 2);
+      if (pm) {
+        const int first = __ffs(pm) - 1;
+        excl += warp_sum(lane < first ? t : lane == first ? (w & VM) : 0ull);
+        break;
+      }
+      excl += warp_sum(t);
+      idx -= 32;
+    }
+    if (lane == 0) {
+      st_relaxed(&st[u], FP | (excl + tot[u]));
+      s_excl = excl;
+    }
+  }
+  __syncthreads();
+  uint32_t wbase = 0;
+  for (int i = 0; i < warp; ++i) wbase += wsum[i];
+  const uint32_t gofs = wbase + inc - c;  // this thread's group: offset within the unit
+  WriteCtx C{Q, urow0, s_excl, Q->capacity, Q->nproj};
+  if (C.excl < C.cap) {
+    uint32_t q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t valid = 0;
+    int nq = 0;
+    const uint32_t *bm = Q->bitmap;
+    for (int gi = 0; gi < 32; ++gi) {  // this warp's groups: 32*warp + gi
+      const int g = warp * 32 + gi;
+      if (g >= ng) break;
+      const uint32_t cnt = __shfl_sync(FULL, c, gi);
+      if (cnt == 0) continue;
+      const uint32_t gpos = __shfl_sync(FULL, gofs, gi);
+      if (C.excl + gpos >= C.cap) continue;
+      const uint32_t word = lane < 8 ? __ldcg(&bm[(size_t)(g0 + g) * 8 + lane]) : 0u;
+      uint32_t bal[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) bal[p] = __shfl_sync(FULL, word, p);
+      const uint32_t grow = (uint32_t)g * kGroup;  // group's first row, unit-relative
+      for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        uint32_t entry = 0;
+        const bool ok = j < cnt;
+        if (ok) {
+          uint32_t cum = 0, sel = 0, r = 0, pp = 0;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const uint32_t cc = __popc(bal[p]);
+            if (j >= cum && j < cum + cc) {
+              sel = bal[p];
+              r = j - cum;
+              pp = (uint32_t)p;
+            }
+            cum += cc;
+          }
+          entry = ((grow + 32u * pp + nth_set_bit(sel, r)) << 16) | (gpos + j);
+        }
+#pragma unroll
+        for (int k = 7; k > 0; --k) q[k] = q[k - 1];
+        q[0] = entry;
+        valid = (valid << 1) | (ok ? 1u : 0u);
+        if (++nq == 8) {
+          flush_queue(C, q, valid);
+          nq = 0;
+          valid = 0;
+        }
+      }
+    }
+    if (nq) flush_queue(C, q, valid & ((1u << nq) - 1u));
+  }
+  // per-query completion time: the last write block of the query
+  if (Q->done_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
+    }
   }
 }
 
@@ -1008,6 +965,29 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
   return ESC_OK;
 }
 
+esc_status launch_write(const Launch &L, uint32_t blocks, cudaStream_t st) {
+  if (blocks == 0) return ESC_OK;
+  write_kernel<<<blocks, kWriteThreads, 0, st>>>(L);
+  ESC_CK(cudaGetLastError());
+  return ESC_OK;
+}
+
+// Compaction scratch of one query: unit totals and look-back words (both
+// zeroed before the scan), then the selection bitmap and group counts (fully
+// written by the scan before the write kernel reads them).
+size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
+size_t select_other_bytes(const Query &q) {
+  const size_t groups = (size_t)q.ntiles * q.gmax;
+  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255);
+}
+void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
+  q.unit_total = reinterpret_cast<unsigned long long *>(zeroed);
+  q.unit_status = q.unit_total + q.nunits;
+  const size_t groups = (size_t)q.ntiles * q.gmax;
+  q.bitmap = reinterpret_cast<uint32_t *>(other);
+  q.gcounts = reinterpret_cast<uint32_t *>(other + ((groups * 32 + 255) & ~(size_t)255));
+}
+
 // Validates a (table, pred, rows) call and fills the per-call query.
 esc_status prepare_query(const esc_table *t, const esc_pred *p, const esc_rows *rows, int mode, Query *q) {
   if (!t || !p) return fail(ESC_EINVAL, "table and predicate are required");
@@ -1019,7 +999,7 @@ esc_status prepare_query(const esc_table *t, const esc_pred *p, const esc_rows *
   fill_query_program(p, q);
   q->nrows = (uint32_t)t->nrows;
   q->mode = mode;
-  if (mode == MODE_COMPACT) {
+  if (mode == MODE_SELECT) {
     if (!rows) return fail(ESC_EINVAL, "rows is NULL");
     if (rows->capacity > 0 && !rows->row_ids) return fail(ESC_EINVAL, "rows->row_ids is NULL");
     if (q->nproj > 0 && rows->capacity > 0 && !rows->proj) return fail(ESC_EINVAL, "rows->proj is NULL");
@@ -1057,13 +1037,14 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.q0.bitmap = bitmap;
   L.nq = 1;
   L.total_units = L.q0.nunits;
-  // scratch: header + count, then (compaction) one look-back word per unit; all zeroed
+  // scratch: header + count, then (compaction) unit totals and look-back
+  // words (zeroed with the header), then the selection bitmap and group counts
   const size_t head = (sizeof(SingleScratch) + 255) & ~(size_t)255;
-  const size_t status_bytes = mode == MODE_COMPACT ? (((size_t)L.q0.nunits * 8 + 255) & ~(size_t)255) : 0;
-  const size_t bytes = head + status_bytes;
+  const size_t zeroed = mode == MODE_SELECT ? select_zeroed_bytes(L.q0) : 0;
+  const size_t other = mode == MODE_SELECT ? select_other_bytes(L.q0) : 0;
   void *mem = nullptr;
-  if ((s = alloc_async(&mem, bytes, st)) != ESC_OK) return s;
-  cudaError_t e = cudaMemsetAsync(mem, 0, head + status_bytes, st);
+  if ((s = alloc_async(&mem, head + zeroed + other, st)) != ESC_OK) return s;
+  cudaError_t e = cudaMemsetAsync(mem, 0, head + zeroed, st);
   if (e == cudaSuccess && dev_count) e = cudaMemsetAsync(dev_count, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, st);
@@ -1073,8 +1054,9 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   SingleScratch *sc = static_cast<SingleScratch *>(mem);
   L.hdr = &sc->hdr;
   L.q0.count = dev_count ? dev_count : &sc->count;
-  if (mode == MODE_COMPACT) L.q0.unit_status = reinterpret_cast<unsigned long long *>(base + head);
+  if (mode == MODE_SELECT) select_bind(L.q0, base + head, base + head + zeroed);
   s = launch_scan(L, st);
+  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
     return s;
@@ -1106,7 +1088,7 @@ esc_status esc_selectivity(const esc_table *t, const esc_pred *p, uint64_t *coun
   if (!count) return fail(ESC_EINVAL, "esc_selectivity: count is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SingleScratch *sc = nullptr;
-  esc_status s = run_single(t, p, rows, rows ? MODE_COMPACT : MODE_COUNT, nullptr, nullptr, st, &sc);
+  esc_status s = run_single(t, p, rows, rows ? MODE_SELECT : MODE_COUNT, nullptr, nullptr, st, &sc);
   if (s != ESC_OK) return s;
   uint64_t c = 0;
   if ((s = finish_single(sc, &c, st)) != ESC_OK) return s;
@@ -1124,7 +1106,7 @@ esc_status esc_selectivity_async(const esc_table *t, const esc_pred *p, uint64_t
   if (!dev_count) return fail(ESC_EINVAL, "esc_selectivity_async: dev_count is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SingleScratch *sc = nullptr;
-  esc_status s = run_single(t, p, rows, rows ? MODE_COMPACT : MODE_COUNT, nullptr,
+  esc_status s = run_single(t, p, rows, rows ? MODE_SELECT : MODE_COUNT, nullptr,
                             reinterpret_cast<unsigned long long *>(dev_count), st, &sc);
   if (s != ESC_OK) return s;
   cudaError_t e = cudaFreeAsync(sc, st);
@@ -1155,14 +1137,15 @@ struct esc_batch {
   int32_t n = 0;
   int device = 0;
   uint32_t total_units = 0;
+  uint32_t write_blocks = 0;
   void *dev_mem = nullptr;          // queries + scratch, owned
   Query *queries = nullptr;         // device
-  uint8_t *scratch = nullptr;       // device: hdr, counts, done, tiles_left, look-back words
+  uint8_t *scratch = nullptr;       // device: hdr, counts, done, countdowns, unit words
   size_t scratch_bytes = 0;
   unsigned long long *counts = nullptr;
   unsigned long long *done = nullptr;
   unsigned int *tiles_left = nullptr;
-  unsigned int *tiles_init = nullptr;  // device copy of each query's tile count
+  unsigned int *tiles_init = nullptr;  // device copy of each query's countdown start
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -1190,16 +1173,21 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
-  uint64_t units = 0, status_words = 0;
+  uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
-    if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_COMPACT : MODE_COUNT,
+    if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
                            &qs[i])) != ESC_OK)
       return s;
     qs[i].unit_base = (uint32_t)units;
+    qs[i].wunit_base = (uint32_t)wunits;
     units += qs[i].nunits;
-    if (compact) status_words += qs[i].nunits;
+    if (compact) {
+      wunits += qs[i].nunits;
+      zeroed += select_zeroed_bytes(qs[i]);
+      other += select_other_bytes(qs[i]);
+    }
     if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
   }
   esc_batch *b = new (std::nothrow) esc_batch;
@@ -1207,13 +1195,16 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   b->n = n;
   cudaGetDevice(&b->device);
   b->total_units = (uint32_t)units;
-  const size_t q_bytes = sizeof(Query) * (size_t)n;
+  b->write_blocks = (uint32_t)wunits;
+  // device memory: queries | zeroed every run: header, counts, done times,
+  // countdowns, unit totals + look-back words | countdown initial values |
+  // selection bitmaps + group counts
+  const size_t q_span = (sizeof(Query) * (size_t)n + 255) & ~(size_t)255;
   const size_t hdr_bytes = 256;
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
-  b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + status_words * 8;  // zeroed every run
-  const size_t q_span = (q_bytes + 255) & ~(size_t)255;
-  const size_t total = q_span + b->scratch_bytes + left_bytes;
+  b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + (size_t)zeroed;
+  const size_t total = q_span + b->scratch_bytes + left_bytes + (size_t)other;
   cudaError_t e = cudaMalloc(&b->dev_mem, total);
   if (e != cudaSuccess) {
     batch_free(b);
@@ -1225,32 +1216,34 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   b->counts = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes);
   b->done = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes + cnt_bytes);
   b->tiles_left = reinterpret_cast<unsigned int *>(b->scratch + hdr_bytes + 2 * cnt_bytes);
-  unsigned long long *status = reinterpret_cast<unsigned long long *>(b->scratch + hdr_bytes + 2 * cnt_bytes + left_bytes);
+  uint8_t *zp = b->scratch + hdr_bytes + 2 * cnt_bytes + left_bytes;
   b->tiles_init = reinterpret_cast<unsigned int *>(b->scratch + b->scratch_bytes);
-  if (((uintptr_t)b->tiles_init + left_bytes) > (uintptr_t)base + total) {
-    batch_free(b);
-    return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
-  }
+  uint8_t *op = b->scratch + b->scratch_bytes + left_bytes;
   std::vector<unsigned int> init((size_t)n);
-  uint64_t so = 0;
   for (int i = 0; i < n; ++i) {
     qs[i].count = &b->counts[i];
     qs[i].done_ns = &b->done[i];
     qs[i].tiles_left = &b->tiles_left[i];
-    if (qs[i].mode == MODE_COMPACT) {
-      qs[i].unit_status = status + so;
-      so += qs[i].nunits;
+    if (qs[i].mode == MODE_SELECT) {
+      select_bind(qs[i], zp, op);
+      zp += select_zeroed_bytes(qs[i]);
+      op += select_other_bytes(qs[i]);
+      init[i] = qs[i].nunits;                        // counted down by the write kernel
+    } else {
+      init[i] = qs[i].ntiles * (unsigned)kConsumers;  // counted down by the scan kernel
     }
-    init[i] = qs[i].ntiles * (unsigned)kConsumers;
   }
-
-  e = cudaMemcpy(b->queries, qs.data(), q_bytes, cudaMemcpyHostToDevice);
+  if ((uintptr_t)op > (uintptr_t)base + total) {
+    batch_free(b);
+    return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
+  }
+  e = cudaMemcpy(b->queries, qs.data(), sizeof(Query) * (size_t)n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->tiles_init, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     batch_free(b);
     return fail(ESC_ECUDA, std::string("esc_batch_prepare: cudaMemcpy: ") + cudaGetErrorString(e));
   }
-  // Capture reset + launch into a graph once; runs replay it.
+  // Capture reset + scan + write into a graph once; runs replay it.
   cudaStream_t cs;
   e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -1269,6 +1262,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
     ls = launch_scan(L, cs);
+    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
   if (e == cudaSuccess && ls == ESC_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
