@@ -142,6 +142,26 @@ esc_status esc_selectivity(const esc_table *table, const esc_pred *pred, uint64_
 esc_status esc_selectivity_async(const esc_table *table, const esc_pred *pred,
                                  uint64_t *dev_count, esc_rows *rows, void *stream);
 
+/* Allocation-free form of esc_selectivity, for callers that must not
+ * allocate device memory: code running inside an allocator of its own (a
+ * buffer pool that owns the GPU's memory), code on a latency-critical path
+ * where cudaMalloc and cudaFree would synchronise the device, or host code
+ * that runs where CUDA allocation calls are not allowed.  The paper has no
+ * counterpart; it is an interface convenience of this library.
+ * Same arguments, results and status codes as esc_selectivity.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch is a 12 MiB
+ * array built into the library, reserved on every device that loads the
+ * library until the process exits.  Counting alone fits any table; with
+ * `rows` (materialisation) the table may have up to about 85 million rows
+ * (the scratch needs about nrows/7 bytes); larger tables give ESC_EINVAL.
+ * The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  Every call
+ * shares the one array: calls whose GPU work overlaps (different streams,
+ * or host threads without ordering) race and give wrong results.
+ * Synchronises `stream`. */
+esc_status esc_selectivity_noalloc(const esc_table *table, const esc_pred *pred, uint64_t *count,
+                                   esc_rows *rows, void *stream);
+
 /* Batched sub-queries (Sec. 2: one per table that has a selection): the n
  * pairs (tables[i], preds[i]) run in one persistent kernel launch, captured
  * in a CUDA graph at prepare time.  rows may be NULL (counts only) or an

@@ -1345,3 +1345,127 @@ esc_status esc_selftest_wait_timeout(uint64_t limit_ns, void *stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free variant
+// esc_selectivity_noalloc: the same sub-query for callers that must not
+// allocate device memory.  Its scratch (launch header, count, unit words,
+// selection bitmap, group counts) is one array in this library's device
+// image, sized kNoAllocScratchBytes; the CUDA driver reserves it on every
+// device where the library's kernels are loaded, until the process exits.
+
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)12 << 20;  // 12 MiB
+}  // namespace
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+struct NoAllocDevice {
+  bool ready = false;
+  int sms = 0;
+  int blocks_per_sm = 0;
+  uint8_t *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[64];
+
+struct NoAllocHead {
+  ScratchHdr hdr;
+  unsigned long long count;
+  unsigned long long pad;
+};
+
+// One-time set-up per device, on the current device: kernel attributes and
+// the device address of the scratch array (host code cannot use the array's
+// name as a device pointer).  Allocates nothing.
+esc_status noalloc_device(NoAllocDevice **out) {
+  int dev = 0;
+  ESC_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(ESC_EINVAL, "esc_selectivity_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc[dev];
+  if (!d.ready) {
+    ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
+    if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(ESC_ECUDA, std::string("esc_selectivity_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    d.scratch = static_cast<uint8_t *>(p);
+    d.ready = true;
+  }
+  *out = &d;
+  return ESC_OK;
+}
+
+}  // namespace
+
+extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred *p, uint64_t *count,
+                                              esc_rows *rows, void *stream) {
+  if (!count) return fail(ESC_EINVAL, "esc_selectivity_noalloc: count is NULL");
+  if (!t || !p) return fail(ESC_EINVAL, "esc_selectivity_noalloc: table and predicate are required");
+  if (p->table != t) return fail(ESC_EINVAL, "esc_selectivity_noalloc: predicate was compiled against another table");
+  NoAllocDevice *d;
+  esc_status s = noalloc_device(&d);
+  if (s != ESC_OK) return s;
+  const int mode = rows ? MODE_SELECT : MODE_COUNT;
+  Launch L;
+  std::memset(&L, 0, sizeof L);
+  Query &q = L.q0;
+  fill_query_program(p, &q);
+  q.nrows = (uint32_t)t->nrows;
+  q.mode = mode;
+  if (rows) {
+    if (rows->capacity > 0 && !rows->row_ids) return fail(ESC_EINVAL, "esc_selectivity_noalloc: rows->row_ids is NULL");
+    if (q.nproj > 0 && rows->capacity > 0 && !rows->proj)
+      return fail(ESC_EINVAL, "esc_selectivity_noalloc: rows->proj is NULL");
+    q.out_ids = rows->row_ids;
+    q.capacity = rows->capacity;
+    for (int i = 0; i < q.nproj; ++i) {
+      q.out_proj[i] = rows->capacity ? rows->proj[i] : nullptr;
+      if (rows->capacity && !q.out_proj[i])
+        return fail(ESC_EINVAL, "esc_selectivity_noalloc: a projected output pointer is NULL");
+    }
+  }
+  layout_stage(q, d->sms);
+  L.nq = 1;
+  L.total_units = q.nunits;
+  const size_t head = (sizeof(NoAllocHead) + 255) & ~(size_t)255;
+  const size_t zeroed = mode == MODE_SELECT ? select_zeroed_bytes(q) : 0;
+  const size_t other = mode == MODE_SELECT ? select_other_bytes(q) : 0;
+  if (head + zeroed + other > kNoAllocScratchBytes)
+    return fail(ESC_EINVAL, "esc_selectivity_noalloc: materialising this table needs " +
+                                std::to_string(head + zeroed + other) +
+                                " bytes of scratch, more than the built-in 12 MiB; use esc_selectivity");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear what must start at zero
+  ESC_CK(cudaMemsetAsync(d->scratch, 0, head + zeroed, st));
+  NoAllocHead *h = reinterpret_cast<NoAllocHead *>(d->scratch);
+  L.hdr = &h->hdr;
+  q.count = &h->count;
+  if (mode == MODE_SELECT) select_bind(q, d->scratch + head, d->scratch + head + zeroed);
+  if (L.total_units > 0) {
+    const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), L.total_units);
+    scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
+    ESC_CK(cudaGetLastError());
+    if (mode == MODE_SELECT) {
+      write_kernel<<<q.nunits, kWriteThreads, 0, st>>>(L);
+      ESC_CK(cudaGetLastError());
+    }
+  }
+  NoAllocHead back;
+  ESC_CK(cudaMemcpyAsync(&back, h, sizeof back, cudaMemcpyDeviceToHost, st));
+  ESC_CK(cudaStreamSynchronize(st));
+  if (back.hdr.status != 0) return fail((esc_status)back.hdr.status, "a bounded device-side wait gave up");
+  *count = back.count;
+  if (rows) {
+    rows->written = std::min<uint64_t>(back.count, rows->capacity);
+    if (back.count > rows->capacity)
+      return fail(ESC_ETRUNC, "esc_selectivity_noalloc: more qualifying rows than capacity");
+  }
+  clear_error();
+  return ESC_OK;
+}

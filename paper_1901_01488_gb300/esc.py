@@ -50,6 +50,7 @@ _sig = {
     "esc_predicate_explain": ([_P, ctypes.c_char_p, ctypes.c_uint64], _S),
     "esc_selectivity": ([_P, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(esc_rows), _P], _S),
     "esc_selectivity_async": ([_P, _P, _P, ctypes.POINTER(esc_rows), _P], _S),
+    "esc_selectivity_noalloc": ([_P, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(esc_rows), _P], _S),
     "esc_batch_prepare": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(esc_rows),
                            ctypes.POINTER(_P)], _S),
     "esc_batch_run": ([_P, _P, _P, _P], _S),
@@ -144,6 +145,20 @@ def esc_selectivity(table: int, pred: int, rows=None, stream=None) -> Tuple[int,
     r, keep = _rows_struct(*rows)
     st = _lib.esc_selectivity(table, pred, ctypes.byref(cnt), ctypes.byref(r), _stream(stream))
     _check(st, "esc_selectivity", ok=(ESC_OK, ESC_ETRUNC))
+    return cnt.value, st
+
+
+def esc_selectivity_noalloc(table: int, pred: int, rows=None, stream=None) -> Tuple[int, int]:
+    """Allocation-free esc_selectivity (scratch built into the library).
+    Returns (count, status); status is ESC_OK or ESC_ETRUNC."""
+    cnt = ctypes.c_uint64()
+    if rows is None:
+        st = _lib.esc_selectivity_noalloc(table, pred, ctypes.byref(cnt), None, _stream(stream))
+        _check(st, "esc_selectivity_noalloc")
+        return cnt.value, st
+    r, keep = _rows_struct(*rows)
+    st = _lib.esc_selectivity_noalloc(table, pred, ctypes.byref(cnt), ctypes.byref(r), _stream(stream))
+    _check(st, "esc_selectivity_noalloc", ok=(ESC_OK, ESC_ETRUNC))
     return cnt.value, st
 
 
