@@ -41,7 +41,6 @@ constexpr int kThreads = 32 * (kConsumers + 1);  // + the producer warp: 16 warp
 constexpr int kStages = 3;
 constexpr uint32_t kStageBytes = 64 * 1024;
 constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256: one write-kernel thread per group
-constexpr int kWriteThreads = kMaxUnitGroups;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr uint32_t FULL = 0xffffffffu;
 static_assert(kStageBytes <= 65536, "stage column offsets are 16-bit");
@@ -623,20 +622,27 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   }
 }
 
-// ------------------------------------------------------------------ the write kernel
-// Second pass of ordered compaction: one block per work unit (<= 65536
-// rows, <= 256 groups of 256 rows).  The unit's output offset comes from a
-// decoupled look-back over the units before it (Merrill & Garland 2016):
-// every unit's aggregate is already final (written by the scan kernel), so
-// the look-back adds aggregates until it meets a unit whose inclusive prefix
-// another block has published, and never waits.  Group offsets within the
-// unit come from a block-wide scan of the group counts; each warp then
-// writes its 32 groups' qualifying rows: ids, then every projected column.
+// ------------------------------------------------------------------ the write kernels
+// Second pass of ordered compaction, in two launches.
 //
-// Writes use a gather queue: each group's qualifying rows are spread
-// densely over the lanes (entry j -> lane j % 32) and pushed as packed
-// (row within unit << 16 | slot within unit) into 8 slots per lane; a flush
-// issues all loads of the queued rows for two columns before any store.
+// offsets_kernel: one block per work unit (<= 65536 rows, <= 256 groups of
+// 256 rows).  The unit's output offset comes from a decoupled look-back over
+// the units before it (Merrill & Garland 2016): every unit's aggregate is
+// already final (written by the scan kernel), so the look-back adds
+// aggregates until it meets a unit whose inclusive prefix another block has
+// published, and never waits.  A block-wide scan of the group counts then
+// gives every group's first output slot.
+//
+// gather_kernel: 8 groups per warp, independent of one another.  Dense full
+// groups are read with 16-byte vector loads (lane l: rows 8l .. 8l+7),
+// staged in shared memory at their output slots and stored with lane =
+// output slot; in other groups the j-th qualifying row goes to lane j % 32
+// and is copied directly.
+
+constexpr int kOffsetThreads = 256;   // one thread per group of a unit
+constexpr int kGatherThreads = 256;
+constexpr int kGatherGroupsPerWarp = 8;
+constexpr int kGatherGroups = (kGatherThreads / 32) * kGatherGroupsPerWarp;  // 64 per block
 
 // Position of the r-th set bit (0-based) of x; r < popc(x).
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t r) {
@@ -671,79 +677,81 @@ __device__ __forceinline__ void store_elem(void *base, unsigned long long pos, u
   }
 }
 
-struct WriteCtx {
-  const Query *Q;
-  uint32_t urow0;            // unit's first row
-  unsigned long long excl;   // unit's first output slot
-  uint64_t cap;
-  int np;
-};
-
-__device__ __forceinline__ void flush_queue(const WriteCtx &C, const uint32_t (&q)[8], uint32_t valid) {
+template <int W>
+__device__ __forceinline__ void load8_row_major(const uint8_t *p, uint64_t (&v)[8]) {
+  if (W == 1) {
+    const uint2 x = *reinterpret_cast<const uint2 *>(p);
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (((valid >> k) & 1u) && C.excl + (q[k] & 0xffffu) >= C.cap) valid &= ~(1u << k);
-  uint32_t *ids = C.Q->out_ids;
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if ((valid >> k) & 1u) ids[C.excl + (q[k] & 0xffffu)] = C.urow0 + (q[k] >> 16);
-  for (int c0 = 0; c0 < C.np; c0 += 2) {
-    const int nc = min(2, C.np - c0);
-    uint64_t v[2][8];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (c < nc) {
-        const int w = C.Q->proj_w[c0 + c];
-        const uint8_t *src = C.Q->proj_ptr[c0 + c];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if ((valid >> k) & 1u) v[c][k] = load_elem(src, C.urow0 + (q[k] >> 16), w);
-      }
+    for (int k = 0; k < 4; ++k) {
+      v[k] = (x.x >> (8 * k)) & 0xffu;
+      v[k + 4] = (x.y >> (8 * k)) & 0xffu;
     }
+  } else if (W == 2) {
+    const uint4 x = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (c < nc) {
-        const int w = C.Q->proj_w[c0 + c];
-        void *dst = C.Q->out_proj[c0 + c];
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = w[k] & 0xffffu;
+      v[2 * k + 1] = w[k] >> 16;
+    }
+  } else if (W == 4) {
+    const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
+    const uint4 b = reinterpret_cast<const uint4 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if ((valid >> k) & 1u) store_elem(dst, C.excl + (q[k] & 0xffffu), v[c][k], w);
-      }
+    for (int k = 0; k < 4; ++k) {
+      const ulonglong2 x = q[k];
+      v[2 * k] = x.x;
+      v[2 * k + 1] = x.y;
     }
   }
 }
 
-__global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_constant__ Launch L) {
-  __shared__ Query sq;                      // this block's query
-  __shared__ uint32_t wsum[kWriteThreads / 32];
+template <typename T, int W>
+__device__ __forceinline__ void dense_column(const uint8_t *src_rows, T *dst, T *stg, uint32_t bits8, uint32_t excl_l,
+                                             uint32_t cnt, unsigned long long base, uint64_t cap, int lane) {
+  uint64_t v[8];
+  load8_row_major<W>(src_rows + (size_t)lane * 8 * W, v);
+  uint32_t r = excl_l;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((bits8 >> k) & 1u) stg[r++] = (T)v[k];
+  __syncwarp();
+  for (uint32_t i = (uint32_t)lane; i < cnt; i += 32)
+    if (base + i < cap) dst[base + i] = stg[i];
+  __syncwarp();
+}
+
+// Finds the query a block belongs to: the last one whose first block (the
+// field `base` selects) is <= blockIdx.x.
+template <typename F>
+__device__ __forceinline__ int block_query(const Launch &L, F base) {
+  int lo = 0, hi = L.nq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base(query_ptr(L, mid)) <= blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kOffsetThreads) offsets_kernel(const __grid_constant__ Launch L) {
+  __shared__ uint32_t wsum[kOffsetThreads / 32];
   __shared__ unsigned long long s_excl;
   __shared__ int s_q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  // which query (batches: the last one whose first write block is <= blockIdx.x)
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = L.nq - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (query_ptr(L, mid)->wunit_base <= blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    s_q = lo;
-  }
+  if (threadIdx.x == 0) s_q = block_query(L, [](const Query *q) { return q->wunit_base; });
   __syncthreads();
-  {
-    const uint2 *src = reinterpret_cast<const uint2 *>(query_ptr(L, s_q));
-    uint2 *dst = reinterpret_cast<uint2 *>(&sq);
-    for (int i = threadIdx.x; i < (int)(sizeof(Query) / 8); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  const Query *Q = &sq;
+  const Query *Q = query_ptr(L, s_q);
   const uint32_t u = blockIdx.x - Q->wunit_base;
   const uint32_t urows = Q->unit_tiles * Q->tile_rows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
   const int ng = (int)((rows + kGroup - 1) / kGroup);
   const uint32_t g0 = urow0 / kGroup;
-  // block-wide exclusive scan of the group counts (one group per thread)
   const uint32_t c = (int)threadIdx.x < ng ? Q->gcounts[g0 + threadIdx.x] : 0u;
   uint32_t inc = c;
 #pragma unroll
@@ -752,28 +760,41 @@ __global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_const
     if (lane >= o) inc += y;
   }
   if (lane == 31) wsum[warp] = inc;
-  // look-back for the unit's exclusive prefix (warp 0)
   if (warp == 0) {
+    // 8 predecessor units per lane per round trip; every aggregate is final
     const unsigned long long FP = 2ull << 62, VM = (1ull << 62) - 1;
     unsigned long long *st = Q->unit_status;
     const unsigned long long *tot = Q->unit_total;
     unsigned long long excl = 0;
-    long long idx = (long long)u - 1;
+    long long idx = (long long)u - 1;  // closest predecessor not yet accounted
     while (idx >= 0) {
-      const long long j = idx - lane;
-      unsigned long long w = FP, t = 0;
-      if (j >= 0) {
-        w = ld_relaxed(&st[j]);
-        t = tot[j];
+      unsigned long long sum = 0, pval = 0;  // this lane: totals before its closest published prefix
+      int kp = 8;                            // index of that prefix among the lane's 8 units, 8 = none
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const long long j = idx - 8 * lane - k;
+        unsigned long long w = FP, t = 0;  // before the first unit: prefix 0
+        if (j >= 0) {
+          w = ld_relaxed(&st[j]);
+          t = tot[j];
+        }
+        if (kp == 8) {
+          if ((w >> 62) == 2) {
+            kp = k;
+            pval = w & VM;
+          } else {
+            sum += t;
+          }
+        }
       }
-      const uint32_t pm = __ballot_sync(FULL, (w >> 62) == 2);
+      const uint32_t pm = __ballot_sync(FULL, kp < 8);
       if (pm) {
         const int first = __ffs(pm) - 1;
-        excl += warp_sum(lane < first ? t : lane == first ? (w & VM) : 0ull);
+        excl += warp_sum(lane < first ? sum : lane == first ? sum + pval : 0ull);
         break;
       }
-      excl += warp_sum(t);
-      idx -= 32;
+      excl += warp_sum(sum);
+      idx -= 256;
     }
     if (lane == 0) {
       st_relaxed(&st[u], FP | (excl + tot[u]));
@@ -783,62 +804,224 @@ __global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_const
   __syncthreads();
   uint32_t wbase = 0;
   for (int i = 0; i < warp; ++i) wbase += wsum[i];
-  const uint32_t gofs = wbase + inc - c;  // this thread's group: offset within the unit
-  WriteCtx C{Q, urow0, s_excl, Q->capacity, Q->nproj};
-  if (C.excl < C.cap) {
-    uint32_t q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t valid = 0;
-    int nq = 0;
-    const uint32_t *bm = Q->bitmap;
-    for (int gi = 0; gi < 32; ++gi) {  // this warp's groups: 32*warp + gi
-      const int g = warp * 32 + gi;
-      if (g >= ng) break;
-      const uint32_t cnt = __shfl_sync(FULL, c, gi);
-      if (cnt == 0) continue;
-      const uint32_t gpos = __shfl_sync(FULL, gofs, gi);
-      if (C.excl + gpos >= C.cap) continue;
-      const uint32_t word = lane < 8 ? __ldcg(&bm[(size_t)(g0 + g) * 8 + lane]) : 0u;
-      uint32_t bal[8];
+  if ((int)threadIdx.x < ng) Q->goff[g0 + threadIdx.x] = s_excl + wbase + inc - c;
+}
+
+// Copies staged sparse entries (row within the warp's groups << 16 | output
+// slot relative to the warp's first group) to the outputs: 4 entries per
+// lane, each column's loads issued before its stores.
+__device__ __forceinline__ void flush_sparse(const struct GatherInfo &G, const uint32_t *ent, uint32_t n,
+                                             uint32_t row_ref, unsigned long long pos_ref, int lane);
+
+// What the gather kernel needs of a query, in shared memory.
+struct GatherInfo {
+  uint64_t capacity;
+  uint32_t *out_ids;
+  const uint32_t *bitmap;
+  const uint32_t *gcounts;
+  const unsigned long long *goff;
+  unsigned int *tiles_left;
+  unsigned long long *done_ns;
+  uint32_t ngroups, nrows, gblock_base;
+  int32_t nproj;
+  uint8_t proj_w[kMaxProj];
+  const uint8_t *proj_ptr[kMaxProj];
+  void *out_proj[kMaxProj];
+};
+
+__device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t *ent, uint32_t n, uint32_t row_ref,
+                                             unsigned long long pos_ref, int lane) {
+  const uint64_t cap = G.capacity;
+  for (uint32_t t0 = 0; t0 < n; t0 += 128) {
+    uint32_t row[4];
+    unsigned long long pos[4];
+    uint32_t ok = 0;
 #pragma unroll
-      for (int p = 0; p < 8; ++p) bal[p] = __shfl_sync(FULL, word, p);
-      const uint32_t grow = (uint32_t)g * kGroup;  // group's first row, unit-relative
-      for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
-        const uint32_t j = j0 + (uint32_t)lane;
-        uint32_t entry = 0;
-        const bool ok = j < cnt;
-        if (ok) {
-          uint32_t cum = 0, sel = 0, r = 0, pp = 0;
-#pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const uint32_t cc = __popc(bal[p]);
-            if (j >= cum && j < cum + cc) {
-              sel = bal[p];
-              r = j - cum;
-              pp = (uint32_t)p;
-            }
-            cum += cc;
-          }
-          entry = ((grow + 32u * pp + nth_set_bit(sel, r)) << 16) | (gpos + j);
-        }
-#pragma unroll
-        for (int k = 7; k > 0; --k) q[k] = q[k - 1];
-        q[0] = entry;
-        valid = (valid << 1) | (ok ? 1u : 0u);
-        if (++nq == 8) {
-          flush_queue(C, q, valid);
-          nq = 0;
-          valid = 0;
-        }
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t t = t0 + 32u * k + (uint32_t)lane;
+      row[k] = 0;
+      pos[k] = 0;
+      if (t < n) {
+        const uint32_t e = ent[t];
+        row[k] = row_ref + (e >> 16);
+        pos[k] = pos_ref + (e & 0xffffu);
+        if (pos[k] < cap) ok |= 1u << k;
       }
     }
-    if (nq) flush_queue(C, q, valid & ((1u << nq) - 1u));
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if ((ok >> k) & 1u) G.out_ids[pos[k]] = row[k];
+    for (int c = 0; c < G.nproj; ++c) {
+      const int w = G.proj_w[c];
+      const uint8_t *src = G.proj_ptr[c];
+      void *dst = G.out_proj[c];
+      uint64_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((ok >> k) & 1u) v[k] = load_elem(src, row[k], w);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((ok >> k) & 1u) store_elem(dst, pos[k], v[k], w);
+    }
   }
-  // per-query completion time: the last write block of the query
-  if (Q->done_ns) {
+}
+
+__global__ void __launch_bounds__(kGatherThreads) gather_kernel(const __grid_constant__ Launch L) {
+  __shared__ GatherInfo G;
+  __shared__ unsigned long long stage_buf[kGatherThreads / 32][kGroup];  // per-warp staging (dense groups)
+  __shared__ int s_q;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_q = block_query(L, [](const Query *q) { return q->gblock_base; });
+  __syncthreads();
+  if (warp == 0) {
+    const Query *Q = query_ptr(L, s_q);
+    const int np = Q->nproj;
+    if (lane == 0) {
+      G.capacity = Q->capacity;
+      G.out_ids = Q->out_ids;
+      G.bitmap = Q->bitmap;
+      G.gcounts = Q->gcounts;
+      G.goff = Q->goff;
+      G.tiles_left = Q->tiles_left;
+      G.done_ns = Q->done_ns;
+      G.ngroups = Q->ngroups;
+      G.nrows = Q->nrows;
+      G.gblock_base = Q->gblock_base;
+      G.nproj = np;
+    }
+    if (lane < np) {
+      G.proj_w[lane] = Q->proj_w[lane];
+      G.proj_ptr[lane] = Q->proj_ptr[lane];
+      G.out_proj[lane] = Q->out_proj[lane];
+    }
+  }
+  __syncthreads();
+  const uint64_t cap = G.capacity;
+  const int np = G.nproj;
+  const uint32_t wg0 = (blockIdx.x - G.gblock_base) * kGatherGroups + (uint32_t)warp * kGatherGroupsPerWarp;
+  // this warp's 8 groups: counts and offsets (lanes 0..7), bitmap words (lane 8i+p: group i, word p)
+  const uint32_t gl = wg0 + (uint32_t)(lane & 7);
+  uint32_t cnt_l = 0;
+  unsigned long long off_l = 0;
+  if (lane < 8 && gl < G.ngroups) {
+    cnt_l = G.gcounts[gl];
+    off_l = G.goff[gl];
+  }
+  const uint32_t ga = wg0 + (uint32_t)(lane >> 3), gb = ga + 4;
+  const uint32_t wa = ga < G.ngroups ? __ldcg(&G.bitmap[(size_t)ga * 8 + (lane & 7)]) : 0u;
+  const uint32_t wb = gb < G.ngroups ? __ldcg(&G.bitmap[(size_t)gb * 8 + (lane & 7)]) : 0u;
+  // sparse entries staged in the warp's buffer, relative to the warp's first group
+  const uint32_t row_ref = wg0 * kGroup;
+  const unsigned long long pos_ref = __shfl_sync(FULL, off_l, 0);
+  uint32_t *ent = reinterpret_cast<uint32_t *>(stage_buf[warp]);
+  uint32_t nent = 0;
+  for (int i = 0; i < kGatherGroupsPerWarp; ++i) {
+    const uint32_t g = wg0 + (uint32_t)i;
+    if (g >= G.ngroups) break;
+    const uint32_t cnt = __shfl_sync(FULL, cnt_l, i);
+    if (cnt == 0) continue;
+    const unsigned long long base = __shfl_sync(FULL, off_l, i);
+    if (base >= cap) continue;
+    uint32_t bal[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) bal[p] = __shfl_sync(FULL, i < 4 ? wa : wb, 8 * (i & 3) + p);
+    const uint32_t grow = g * kGroup;  // table row of the group's first row
+    if (cnt > 96 && grow + kGroup <= G.nrows) {
+      if (nent) {  // the staging buffer is needed: write the staged sparse entries first
+        __syncwarp();
+        flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
+        __syncwarp();
+        nent = 0;
+      }
+      const uint32_t wsel = lane >> 2;
+      const uint32_t word = wsel == 0 ? bal[0] : wsel == 1 ? bal[1] : wsel == 2 ? bal[2] : wsel == 3 ? bal[3]
+                          : wsel == 4 ? bal[4] : wsel == 5 ? bal[5] : wsel == 6 ? bal[6] : bal[7];
+      const uint32_t bits8 = (word >> (8 * (lane & 3))) & 0xffu;
+      const uint32_t cl = __popc(bits8);
+      uint32_t incl = cl;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t excl_l = incl - cl;
+      {
+        uint32_t *sids = reinterpret_cast<uint32_t *>(stage_buf[warp]);
+        uint32_t r = excl_l;
+        const uint32_t row_l = grow + 8u * (uint32_t)lane;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if ((bits8 >> k) & 1u) sids[r++] = row_l + (uint32_t)k;
+        __syncwarp();
+        for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
+          if (base + t < cap) G.out_ids[base + t] = sids[t];
+        __syncwarp();
+      }
+      for (int c = 0; c < np; ++c) {
+        const int w = G.proj_w[c];
+        const uint8_t *src = G.proj_ptr[c] + (size_t)grow * w;
+        void *dst = G.out_proj[c];
+        switch (w) {
+          case 1:
+            dense_column<uint8_t, 1>(src, static_cast<uint8_t *>(dst), reinterpret_cast<uint8_t *>(stage_buf[warp]),
+                                     bits8, excl_l, cnt, base, cap, lane);
+            break;
+          case 2:
+            dense_column<uint16_t, 2>(src, static_cast<uint16_t *>(dst),
+                                      reinterpret_cast<uint16_t *>(stage_buf[warp]), bits8, excl_l, cnt, base, cap,
+                                      lane);
+            break;
+          case 4:
+            dense_column<uint32_t, 4>(src, static_cast<uint32_t *>(dst),
+                                      reinterpret_cast<uint32_t *>(stage_buf[warp]), bits8, excl_l, cnt, base, cap,
+                                      lane);
+            break;
+          default:
+            dense_column<unsigned long long, 8>(src, static_cast<unsigned long long *>(dst), stage_buf[warp], bits8,
+                                                excl_l, cnt, base, cap, lane);
+            break;
+        }
+      }
+      continue;
+    }
+    // the group's j-th qualifying row: entry nent + j of the staging buffer
+    if (nent + cnt > 256) {
+      __syncwarp();
+      flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
+      __syncwarp();
+      nent = 0;
+    }
+    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+      const uint32_t j = j0 + (uint32_t)lane;
+      if (j < cnt) {
+        uint32_t cum = 0, sel = 0, r = 0, pp = 0;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const uint32_t cc = __popc(bal[p]);
+          if (j >= cum && j < cum + cc) {
+            sel = bal[p];
+            r = j - cum;
+            pp = (uint32_t)p;
+          }
+          cum += cc;
+        }
+        const uint32_t row = grow + 32u * pp + nth_set_bit(sel, r);
+        ent[nent + j] = ((row - row_ref) << 16) | (uint32_t)(base - pos_ref + j);
+      }
+    }
+    nent += cnt;
+  }
+  if (nent) {
+    __syncwarp();
+    flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
+  }
+  // per-query completion time: the query's last gather block
+  if (G.done_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
+      if (atomicSub(G.tiles_left, 1u) == 1u) *G.done_ns = globaltimer();
     }
   }
 }
@@ -935,6 +1118,7 @@ void layout_stage(Query &q, int sms) {
   }
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;
   q.gmax = q.tile_rows / kGroup;
+  q.ngroups = (q.nrows + kGroup - 1) / kGroup;
   const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);
   const uint32_t max_ut = (uint32_t)std::max<uint64_t>(
       1, std::min<uint64_t>((512ull * 1024) / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
@@ -965,12 +1149,18 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
   return ESC_OK;
 }
 
-esc_status launch_write(const Launch &L, uint32_t blocks, cudaStream_t st) {
-  if (blocks == 0) return ESC_OK;
-  write_kernel<<<blocks, kWriteThreads, 0, st>>>(L);
+// Second pass of compaction: group offsets (one block per unit), then the
+// gather (one block per 64 groups).
+esc_status launch_write(const Launch &L, uint32_t unit_blocks, uint32_t gather_blocks, cudaStream_t st) {
+  if (unit_blocks == 0) return ESC_OK;
+  offsets_kernel<<<unit_blocks, kOffsetThreads, 0, st>>>(L);
+  ESC_CK(cudaGetLastError());
+  gather_kernel<<<gather_blocks, kGatherThreads, 0, st>>>(L);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
+
+uint32_t gather_blocks_for(const Query &q) { return (q.ngroups + kGatherGroups - 1) / kGatherGroups; }
 
 // Compaction scratch of one query: unit totals and look-back words (both
 // zeroed before the scan), then the selection bitmap and group counts (fully
@@ -978,7 +1168,8 @@ esc_status launch_write(const Launch &L, uint32_t blocks, cudaStream_t st) {
 size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
 size_t select_other_bytes(const Query &q) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
-  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255);
+  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255) +
+         ((groups * 8 + 255) & ~(size_t)255);
 }
 void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   q.unit_total = reinterpret_cast<unsigned long long *>(zeroed);
@@ -986,6 +1177,8 @@ void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
   q.bitmap = reinterpret_cast<uint32_t *>(other);
   q.gcounts = reinterpret_cast<uint32_t *>(other + ((groups * 32 + 255) & ~(size_t)255));
+  q.goff = reinterpret_cast<unsigned long long *>(other + ((groups * 32 + 255) & ~(size_t)255) +
+                                                  ((groups * 4 + 255) & ~(size_t)255));
 }
 
 // Validates a (table, pred, rows) call and fills the per-call query.
@@ -1056,7 +1249,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.q0.count = dev_count ? dev_count : &sc->count;
   if (mode == MODE_SELECT) select_bind(L.q0, base + head, base + head + zeroed);
   s = launch_scan(L, st);
-  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
+  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, gather_blocks_for(L.q0), st);
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
     return s;
@@ -1138,6 +1331,7 @@ struct esc_batch {
   int device = 0;
   uint32_t total_units = 0;
   uint32_t write_blocks = 0;
+  uint32_t gather_blocks = 0;
   void *dev_mem = nullptr;          // queries + scratch, owned
   Query *queries = nullptr;         // device
   uint8_t *scratch = nullptr;       // device: hdr, counts, done, countdowns, unit words
@@ -1173,7 +1367,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
-  uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
+  uint64_t units = 0, wunits = 0, gblocks = 0, zeroed = 0, other = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
@@ -1182,9 +1376,11 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       return s;
     qs[i].unit_base = (uint32_t)units;
     qs[i].wunit_base = (uint32_t)wunits;
+    qs[i].gblock_base = (uint32_t)gblocks;
     units += qs[i].nunits;
     if (compact) {
       wunits += qs[i].nunits;
+      gblocks += gather_blocks_for(qs[i]);
       zeroed += select_zeroed_bytes(qs[i]);
       other += select_other_bytes(qs[i]);
     }
@@ -1196,6 +1392,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   cudaGetDevice(&b->device);
   b->total_units = (uint32_t)units;
   b->write_blocks = (uint32_t)wunits;
+  b->gather_blocks = (uint32_t)gblocks;
   // device memory: queries | zeroed every run: header, counts, done times,
   // countdowns, unit totals + look-back words | countdown initial values |
   // selection bitmaps + group counts
@@ -1228,7 +1425,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
-      init[i] = qs[i].nunits;                        // counted down by the write kernel
+      init[i] = gather_blocks_for(qs[i]);            // counted down by the gather kernel
     } else {
       init[i] = qs[i].ntiles * (unsigned)kConsumers;  // counted down by the scan kernel
     }
@@ -1262,7 +1459,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
     ls = launch_scan(L, cs);
-    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
+    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, b->gather_blocks, cs);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
   if (e == cudaSuccess && ls == ESC_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -1452,7 +1649,9 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
     scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
-      write_kernel<<<q.nunits, kWriteThreads, 0, st>>>(L);
+      offsets_kernel<<<q.nunits, kOffsetThreads, 0, st>>>(L);
+      ESC_CK(cudaGetLastError());
+      gather_kernel<<<(q.ngroups + kGatherGroups - 1) / kGatherGroups, kGatherThreads, 0, st>>>(L);
       ESC_CK(cudaGetLastError());
     }
   }
