@@ -457,6 +457,28 @@ struct Lowerer {
   }
 };
 
+// Rough evaluation cost of a subtree in units of one 32-bit range test.
+double cost(const Low &l) {
+  switch (l.kind) {
+    case Low::LEAF:
+      if (l.leaf.op == OP_UDF) return 6.0;
+      if (l.leaf.op == OP_IN) {
+        bool small = true;
+        for (int64_t v : l.vals) small = small && v >= 0 && v < 256;
+        return small ? 1.5 : 1.0 + 0.25 * (double)l.vals.size();
+      }
+      return 1.0;  // range
+    case Low::NOT: return cost(l.kids[0]);
+    case Low::AND:
+    case Low::OR: {
+      double c = 0;
+      for (auto &k : l.kids) c += cost(k) + 0.2;
+      return c;
+    }
+    default: return 0.1;
+  }
+}
+
 int need(const Low &l) {
   switch (l.kind) {
     case Low::NOT: return need(l.kids[0]);
@@ -476,6 +498,7 @@ int need(const Low &l) {
 struct Emitter {
   esc_pred *p;
   std::vector<int> slot_of_col;
+  bool su_only = false;  // order every AND/OR deepest first
 
   int slot(int col) {
     if (slot_of_col[col] < 0) {
@@ -509,15 +532,38 @@ struct Emitter {
         return;
       case Low::AND:
       case Low::OR: {
-        std::vector<std::pair<int, size_t>> order;
-        for (size_t i = 0; i < l.kids.size(); ++i) order.push_back({-need(l.kids[i]), i});
+        // Children cheapest first, so that a cheap test decides as many rows as
+        // possible before the costly ones run; if that order would need more
+        // than kMaxDepth stack entries, deepest first (Sethi-Ullman).  Before
+        // each later child that is costly enough, a conditional jump skips it
+        // and the combining op when the result so far already decides the
+        // connective for all rows a warp holds.
+        std::vector<std::pair<double, size_t>> order;
+        for (size_t i = 0; i < l.kids.size(); ++i) order.push_back({cost(l.kids[i]), i});
         std::stable_sort(order.begin(), order.end());
+        int depth = 0;
+        for (size_t j = 0; j < order.size(); ++j)
+          depth = std::max(depth, need(l.kids[order[j].second]) + (j > 0 ? 1 : 0));
+        if (su_only || depth > kMaxDepth) {
+          order.clear();
+          for (size_t i = 0; i < l.kids.size(); ++i) order.push_back({(double)-need(l.kids[i]), i});
+          std::stable_sort(order.begin(), order.end());
+        }
         for (size_t j = 0; j < order.size(); ++j) {
+          size_t jump = 0;
+          const bool skippable = j > 0 && cost(l.kids[order[j].second]) >= 2.0;
+          if (skippable) {
+            Instr jz{};
+            jz.op = l.kind == Low::AND ? OP_JZ : OP_JNZ;
+            jump = p->code.size();
+            push(jz);
+          }
           emit(l.kids[order[j].second]);
           if (j > 0) {
             Instr c{};
             c.op = l.kind == Low::AND ? OP_AND : OP_OR;
             push(c);
+            if (skippable) p->code[jump].off = (uint16_t)p->code.size();
           }
         }
         return;
@@ -538,8 +584,22 @@ struct Emitter {
           pool((int64_t)s2);
         } else if (ins.op == OP_IN) {
           ins.n = (uint16_t)l.vals.size();
-          ins.off = (uint16_t)p->pool.size();
-          for (int64_t v : l.vals) pool(v);
+          bool small = true;
+          for (int64_t v : l.vals) small = small && v >= 0 && v < 256;
+          if (small) {
+            // 256-bit membership set: bit v of word v / 32, two words per pool entry
+            uint32_t words[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int64_t v : l.vals) words[v >> 5] |= 1u << (v & 31);
+            ins.op = OP_INSET;
+            ins.off = (uint16_t)p->pool.size();
+            for (int k = 0; k < 4; ++k) pool((int64_t)(((uint64_t)words[2 * k + 1] << 32) | words[2 * k]));
+            // the values themselves follow, for the program listing
+            ins.lo = (int64_t)p->pool.size();
+            for (int64_t v : l.vals) pool(v);
+          } else {
+            ins.off = (uint16_t)p->pool.size();
+            for (int64_t v : l.vals) pool(v);
+          }
         }
         push(ins);
         return;
@@ -547,6 +607,23 @@ struct Emitter {
     }
   }
 };
+
+// Largest evaluation-stack depth the program reaches (jumps never skip a push
+// without its matching pop, so straight-line simulation is exact).
+int stack_depth(const std::vector<Instr> &code) {
+  int d = 0, m = 0;
+  for (const Instr &I : code) {
+    switch (I.op) {
+      case OP_AND:
+      case OP_OR: --d; break;
+      case OP_NOT:
+      case OP_JZ:
+      case OP_JNZ: break;
+      default: m = std::max(m, ++d); break;
+    }
+  }
+  return m;
+}
 
 }  // namespace
 
@@ -651,10 +728,19 @@ esc_status esc_predicate_compile(const esc_table *t, const char *text, const cha
     auto ast = parser.parse();
     Lowerer lw{t};
     Low low = lw.lower(*ast);
-    p->depth = need(low);
-    if (p->depth > kMaxDepth) throw ParseError{"predicate nests too deeply (needs more than 8 stack entries)"};
+    if (need(low) > kMaxDepth) throw ParseError{"predicate nests too deeply (needs more than 8 stack entries)"};
     Emitter em{p.get(), std::vector<int>(t->names.size(), -1)};
     em.emit(low);
+    p->depth = stack_depth(p->code);
+    if (p->depth > kMaxDepth) {  // the cheapest-first order went too deep: deepest first everywhere
+      p->code.clear();
+      p->pool.clear();
+      p->ref_cols.clear();
+      em = Emitter{p.get(), std::vector<int>(t->names.size(), -1)};
+      em.su_only = true;
+      em.emit(low);
+      p->depth = stack_depth(p->code);
+    }
     p->ninstr = (int32_t)p->code.size();
     for (int i = 0; i < nproj; ++i) {
       if (!proj[i]) throw ParseError{"projected column name is NULL"};
@@ -717,6 +803,19 @@ esc_status esc_predicate_explain(const esc_pred *p, char *buf, uint64_t buflen) 
         std::snprintf(line, sizeof line, "instr %d UDF %d %s %d %s %" PRId64 " %" PRId64 " %" PRId64 "\n", pc, I.ref,
                       dtype_name(I.dtype), I.ref2, dtype_name(I.dtype2), p->pool[I.off], I.lo, I.hi);
         break;
+      case OP_INSET: {
+        std::snprintf(line, sizeof line, "instr %d IN %d %s", pc, I.ref, dtype_name(I.dtype));
+        s += line;
+        for (int k = 0; k < I.n; ++k) {
+          std::snprintf(line, sizeof line, "%s%" PRId64, k ? "," : " ", p->pool[I.lo + k]);
+          s += line;
+        }
+        line[0] = '\n';
+        line[1] = 0;
+        break;
+      }
+      case OP_JZ: std::snprintf(line, sizeof line, "instr %d JZ %d\n", pc, I.off); break;
+      case OP_JNZ: std::snprintf(line, sizeof line, "instr %d JNZ %d\n", pc, I.off); break;
       case OP_AND: std::snprintf(line, sizeof line, "instr %d AND\n", pc); break;
       case OP_OR: std::snprintf(line, sizeof line, "instr %d OR\n", pc); break;
       case OP_NOT: std::snprintf(line, sizeof line, "instr %d NOT\n", pc); break;

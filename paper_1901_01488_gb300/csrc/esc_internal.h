@@ -42,6 +42,9 @@ enum Op : uint8_t {
   OP_NOT = 5,     // top = ~top
   OP_TRUE = 6,    // push all-ones
   OP_FALSE = 7,   // push zero
+  OP_INSET = 8,   // push  col in a 256-bit set of values 0..255 (8 words at pool[off..off+4))
+  OP_JZ = 9,      // if the top is zero for every row the warp holds, jump to `off` (an AND's result is known)
+  OP_JNZ = 10,    // if the top is all-ones for every row the warp holds, jump to `off` (an OR's result is known)
 };
 
 struct Instr {

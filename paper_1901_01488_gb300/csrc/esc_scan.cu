@@ -260,6 +260,53 @@ __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage
   for (int pc = 0; pc < n; ++pc) {
     const uint4 h = *reinterpret_cast<const uint4 *>(&Q->code[pc]);
     const uint32_t op = h.x & 0xffu;
+    if (op == OP_JZ || op == OP_JNZ) {
+      // the connective's result is already known for every row this warp holds
+      bool done = true;
+      const uint64_t want = op == OP_JZ ? 0u : 0xffu;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) done = done && ((S[i] & 0xffu) == want);
+      if (__all_sync(FULL, done)) pc = (int)(h.z & 0xffffu) - 1;
+      continue;
+    }
+    if (op == OP_INSET) {
+      // membership in a 256-bit set of the values 0..255
+      const int dt = (int)((h.x >> 8) & 0xffu);
+      const int w = width_of(dt);
+      const uint8_t *col = stage + (h.z >> 16);
+      const uint32_t *set = reinterpret_cast<const uint32_t *>(&Q->pool[h.z & 0xffffu]);
+      uint32_t m[NG];
+#pragma unroll
+      for (int i = 0; i < NG; ++i) m[i] = 0;
+      if (dt == ESC_I64) {
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+          int64_t v[8];
+          load8(dt, col + (size_t)grp[i] * kGroup * 8, lane, v);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint64_t x = (uint64_t)v[k];
+            const uint32_t b = x < 256u ? (set[x >> 5] >> (x & 31u)) & 1u : 0u;
+            m[i] |= b << k;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+          int32_t v[8];
+          load8_32(dt, col + (size_t)grp[i] * kGroup * w, lane, v);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t x = (uint32_t)v[k];
+            const uint32_t b = x < 256u ? (set[x >> 5] >> (x & 31u)) & 1u : 0u;
+            m[i] |= b << k;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NG; ++i) S[i] = (S[i] << 8) | m[i];
+      continue;
+    }
     if (op <= OP_UDF) {
       const longlong2 lh = *reinterpret_cast<const longlong2 *>(&Q->code[pc].lo);
       const int dt = (int)((h.x >> 8) & 0xffu);
@@ -1113,7 +1160,7 @@ void layout_stage(Query &q, int sms) {
   }
   for (int pc = 0; pc < q.ninstr; ++pc) {  // resolve operand slots to stage offsets
     Instr &I = q.code[pc];
-    if (I.op == OP_RANGE || I.op == OP_IN || I.op == OP_UDF) I.soff = (uint16_t)q.stage_off[I.ref];
+    if (I.op == OP_RANGE || I.op == OP_IN || I.op == OP_INSET || I.op == OP_UDF) I.soff = (uint16_t)q.stage_off[I.ref];
     if (I.op == OP_UDF) I.soff2 = (uint16_t)q.stage_off[I.ref2];
   }
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;

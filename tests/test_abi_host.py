@@ -68,6 +68,8 @@ def _interpret(listing: str, cols):
                 y = stack.pop(); stack.append(stack.pop() | y)
             elif op == "NOT":
                 stack.append(~stack.pop())
+            elif op in ("JZ", "JNZ"):
+                pass  # skips work only when the result is already decided
             elif op == "TRUE":
                 stack.append(np.ones(n, dtype=bool))
             elif op == "FALSE":
