@@ -178,6 +178,18 @@ esc_status esc_batch_run(esc_batch *batch, uint64_t *dev_counts, uint64_t *dev_d
                          void *stream);
 esc_status esc_batch_destroy(esc_batch *batch);
 
+/* Asynchronous batch without a prepared graph, for a stream of changing
+ * sub-queries (the serving loop): enqueues the n sub-queries as one
+ * persistent scan launch (plus the two compaction launches when any has
+ * rows), with scratch from the library's stream-ordered pool.  Writes n exact
+ * counts to dev_counts and, when dev_done_ns is not NULL, each sub-query's
+ * completion time (%globaltimer).  Does not synchronise; `rows` entries with
+ * capacity 0 and row_ids NULL are count-only; truncation is not reported
+ * (written = min(count, capacity)).  Host arrays may be freed on return. */
+esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc_pred *const *preds,
+                                       int32_t n, const esc_rows *rows, uint64_t *dev_counts,
+                                       uint64_t *dev_done_ns, void *stream);
+
 /* One-shot form of the above: prepares, runs, synchronises and destroys.
  * counts is a host array of n entries. */
 esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred *const *preds,
@@ -207,6 +219,37 @@ esc_status esc_semijoin_counts(const esc_table *fact, const char *const *fk_cols
                                const uint32_t *const *dev_bitmaps, const uint64_t *dim_rows,
                                uint64_t *subset_counts, void *stream);
 
+/* ---------------------------------------------------------------- learned surrogate */
+
+/* A learned selectivity estimator built on top of ESC (not in the paper; the
+ * paper's counts are exact -- this network is trained on them and judged by
+ * them): an MLP 64 -> 128 -> ReLU -> 128 -> ReLU -> 1 mapping encoded
+ * predicate features to log10 selectivity.  Parameters are one flat array
+ * of ESC_MLP_PARAMS floats: W1 [128][64] row-major, b1 [128], W2 [128][128],
+ * b2 [128], w3 [128], b3.  `w_bf16` is a bfloat16 copy of the same array
+ * (the weights the matrix products use; its bias entries are ignored).
+ * All accumulation is float32.  Every pointer is a device pointer; nothing
+ * is synchronised. */
+#define ESC_MLP_PARAMS 24961
+
+/* y[i] = network(x[i]) for `batch` rows of 64 bfloat16 features. */
+esc_status esc_mlp_forward(const uint16_t *x_bf16, uint64_t batch, const uint16_t *w_bf16,
+                           const float *params, float *y, void *stream);
+
+/* Adds to grad[ESC_MLP_PARAMS] the gradient of mean_i (y_i - target_i)^2
+ * over the batch, and to *loss_sum the sum of squared errors.  The caller
+ * zeroes both beforehand. */
+esc_status esc_mlp_grad(const uint16_t *x_bf16, const float *target, uint64_t batch,
+                        const uint16_t *w_bf16, const float *params, float *grad, float *loss_sum,
+                        void *stream);
+
+/* One Adam step (Kingma & Ba 2015) on n float32 parameters with first and
+ * second moments m, v; `step` counts from 1 (bias correction).  Also
+ * refreshes the bfloat16 copy. */
+esc_status esc_mlp_adam(float *params, uint16_t *w_bf16, const float *grad, float *m, float *v,
+                        uint64_t n, float lr, float beta1, float beta2, float eps, int32_t step,
+                        void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Message for the last non-OK status returned to the calling thread. */
@@ -218,6 +261,12 @@ const char *esc_status_string(esc_status status);
  * Integers using Multiplication" (PLDI 1994), Fig. 4.1: for every 64-bit n,
  * t = mulhi(mult, n), n / d = (t + ((n - t) >> sh1)) >> sh2. */
 esc_status esc_udf_magic(uint64_t d, uint64_t *mult, int32_t *sh1, int32_t *sh2);
+
+/* Writes the device's nanosecond clock (%globaltimer, the clock of the
+ * per-sub-query completion times of esc_batch_run) to the device word
+ * *dev_ns when the stream reaches this point.  Not in the paper: used to
+ * measure per-sub-query latency from a common start. */
+esc_status esc_timestamp(uint64_t *dev_ns, void *stream);
 
 /* Runs a one-CTA kernel that waits on a device flag nothing sets, with the
  * same bounded wait the scan kernels use, giving up after about `limit_ns`

@@ -16,7 +16,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libesc.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["esc_scan.cu", "esc_semijoin.cu"]
+CU = ["esc_scan.cu", "esc_semijoin.cu", "esc_mlp.cu"]
 CPP = ["esc_host.cpp"]
 HEADERS = [os.path.join(CSRC, "esc_internal.h"), os.path.join(ROOT, "include", "esc.h")]
 

@@ -1085,6 +1085,8 @@ __global__ void wait_selftest_kernel(const unsigned *flag, ScratchHdr *hdr, uint
   }
 }
 
+__global__ void timestamp_kernel(unsigned long long *out) { *out = globaltimer(); }
+
 // ------------------------------------------------------------------ host side
 namespace {
 
@@ -1566,6 +1568,95 @@ esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred 
     }
   if (trunc) return fail(ESC_ETRUNC, "esc_selectivity_batch: some sub-query had more rows than capacity");
   clear_error();
+  return ESC_OK;
+}
+
+esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
+                                       const esc_rows *rows, uint64_t *dev_counts, uint64_t *dev_done_ns,
+                                       void *stream) {
+  if (n < 1 || !tables || !preds || !dev_counts)
+    return fail(ESC_EINVAL, "esc_selectivity_batch_async: need n >= 1 tables, predicates and dev_counts");
+  std::vector<Query> qs((size_t)n);
+  uint64_t units = 0, wunits = 0, gblocks = 0, zeroed = 0, other = 0;
+  esc_status s;
+  for (int i = 0; i < n; ++i) {
+    const esc_rows *r = rows ? &rows[i] : nullptr;
+    const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
+    if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
+                           &qs[i])) != ESC_OK)
+      return s;
+    qs[i].unit_base = (uint32_t)units;
+    qs[i].wunit_base = (uint32_t)wunits;
+    qs[i].gblock_base = (uint32_t)gblocks;
+    units += qs[i].nunits;
+    if (compact) {
+      wunits += qs[i].nunits;
+      gblocks += gather_blocks_for(qs[i]);
+      zeroed += select_zeroed_bytes(qs[i]);
+      other += select_other_bytes(qs[i]);
+    }
+    if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_selectivity_batch_async: too many work units");
+  }
+  // device block: queries | zeroed: header, counts, done, countdowns, unit words | bitmaps, group data
+  const size_t q_span = (sizeof(Query) * (size_t)n + 255) & ~(size_t)255;
+  const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
+  const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
+  const size_t zbytes = 256 + 2 * cnt_bytes + left_bytes + (size_t)zeroed;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *mem = nullptr;
+  if ((s = alloc_async(&mem, q_span + zbytes + (size_t)other, st)) != ESC_OK) return s;
+  uint8_t *base = static_cast<uint8_t *>(mem);
+  uint8_t *z = base + q_span;
+  unsigned long long *counts = reinterpret_cast<unsigned long long *>(z + 256);
+  unsigned long long *done = reinterpret_cast<unsigned long long *>(z + 256 + cnt_bytes);
+  unsigned int *left = reinterpret_cast<unsigned int *>(z + 256 + 2 * cnt_bytes);
+  uint8_t *zp = z + 256 + 2 * cnt_bytes + left_bytes;
+  uint8_t *op = z + zbytes;
+  std::vector<unsigned int> init((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    qs[i].count = &counts[i];
+    qs[i].done_ns = dev_done_ns ? &done[i] : nullptr;
+    qs[i].tiles_left = &left[i];
+    if (qs[i].mode == MODE_SELECT) {
+      select_bind(qs[i], zp, op);
+      zp += select_zeroed_bytes(qs[i]);
+      op += select_other_bytes(qs[i]);
+      init[i] = gather_blocks_for(qs[i]);
+    } else {
+      init[i] = qs[i].ntiles * (unsigned)kConsumers;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(z, 0, zbytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base, qs.data(), sizeof(Query) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dev_done_ns)
+    e = cudaMemcpyAsync(left, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, st);
+    return fail(ESC_ECUDA, std::string("esc_selectivity_batch_async: ") + cudaGetErrorString(e));
+  }
+  Launch L;
+  std::memset(&L, 0, sizeof L);
+  L.queries = reinterpret_cast<const Query *>(base);
+  L.nq = n;
+  L.total_units = (uint32_t)units;
+  L.hdr = reinterpret_cast<ScratchHdr *>(z);
+  s = launch_scan(L, st);
+  if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, (uint32_t)gblocks, st);
+  if (s == ESC_OK) {
+    e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && dev_done_ns)
+      e = cudaMemcpyAsync(dev_done_ns, done, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = fail(ESC_ECUDA, std::string("esc_selectivity_batch_async: ") + cudaGetErrorString(e));
+  }
+  cudaFreeAsync(mem, st);
+  if (s == ESC_OK) clear_error();
+  return s;
+}
+
+esc_status esc_timestamp(uint64_t *dev_ns, void *stream) {
+  if (!dev_ns) return fail(ESC_EINVAL, "esc_timestamp: dev_ns is NULL");
+  timestamp_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<unsigned long long *>(dev_ns));
+  ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
 

@@ -65,6 +65,13 @@ _sig = {
     "esc_udf_magic": ([ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32),
                        ctypes.POINTER(ctypes.c_int32)], _S),
     "esc_selftest_wait_timeout": ([ctypes.c_uint64, _P], _S),
+    "esc_timestamp": ([_P, _P], _S),
+    "esc_selectivity_batch_async": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32,
+                                     ctypes.POINTER(esc_rows), _P, _P, _P], _S),
+    "esc_mlp_forward": ([_P, ctypes.c_uint64, _P, _P, _P, _P], _S),
+    "esc_mlp_grad": ([_P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P], _S),
+    "esc_mlp_adam": ([_P, _P, _P, _P, _P, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, ctypes.c_int32, _P], _S),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -224,6 +231,21 @@ def esc_selectivity_batch(tables: Sequence[int], preds: Sequence[int], rows=None
     return list(counts), st
 
 
+def esc_selectivity_batch_async(tables: Sequence[int], preds: Sequence[int], dev_counts: torch.Tensor,
+                                rows=None, dev_done_ns: Optional[torch.Tensor] = None, stream=None) -> None:
+    n = len(tables)
+    ta = (_P * n)(*tables)
+    pa = (_P * n)(*preds)
+    done = dev_done_ns.data_ptr() if dev_done_ns is not None else None
+    if rows is None:
+        _check(_lib.esc_selectivity_batch_async(ta, pa, n, None, dev_counts.data_ptr(), done, _stream(stream)),
+               "esc_selectivity_batch_async")
+    else:
+        arr, keep = _rows_array(rows)
+        _check(_lib.esc_selectivity_batch_async(ta, pa, n, arr, dev_counts.data_ptr(), done, _stream(stream)),
+               "esc_selectivity_batch_async")
+
+
 def esc_bitmap_build(dim: int, pred: int, dev_bitmap: torch.Tensor, stream=None) -> int:
     cnt = ctypes.c_uint64()
     _check(_lib.esc_bitmap_build(dim, pred, dev_bitmap.data_ptr() if dev_bitmap.numel() else None,
@@ -252,6 +274,33 @@ def esc_udf_magic(d: int) -> Tuple[int, int, int]:
 
 def esc_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
     return _lib.esc_selftest_wait_timeout(limit_ns, _stream(stream))
+
+
+def esc_timestamp(dev_ns: torch.Tensor, stream=None) -> None:
+    _check(_lib.esc_timestamp(dev_ns.data_ptr(), _stream(stream)), "esc_timestamp")
+
+
+MLP_PARAMS = 24961
+
+
+def esc_mlp_forward(x_bf16: torch.Tensor, w_bf16: torch.Tensor, params: torch.Tensor, y: torch.Tensor,
+                    stream=None) -> None:
+    _check(_lib.esc_mlp_forward(x_bf16.data_ptr(), x_bf16.shape[0], w_bf16.data_ptr(), params.data_ptr(),
+                                y.data_ptr(), _stream(stream)), "esc_mlp_forward")
+
+
+def esc_mlp_grad(x_bf16: torch.Tensor, target: torch.Tensor, w_bf16: torch.Tensor, params: torch.Tensor,
+                 grad: torch.Tensor, loss_sum: torch.Tensor, stream=None) -> None:
+    _check(_lib.esc_mlp_grad(x_bf16.data_ptr(), target.data_ptr(), x_bf16.shape[0], w_bf16.data_ptr(),
+                             params.data_ptr(), grad.data_ptr(), loss_sum.data_ptr(), _stream(stream)),
+           "esc_mlp_grad")
+
+
+def esc_mlp_adam(params: torch.Tensor, w_bf16: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+                 lr: float, step: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 stream=None) -> None:
+    _check(_lib.esc_mlp_adam(params.data_ptr(), w_bf16.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(),
+                             params.numel(), lr, beta1, beta2, eps, step, _stream(stream)), "esc_mlp_adam")
 
 
 def esc_last_error() -> str:

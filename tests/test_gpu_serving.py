@@ -1,0 +1,70 @@
+"""Continuous batching: every served result equals the same sub-query run
+alone, and admission never exceeds the device-memory budget."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1901_01488_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def esc():
+    from paper_1901_01488_gb300 import build
+    build.build()
+    from paper_1901_01488_gb300 import esc as m
+    return m
+
+
+def _tables(esc):
+    sizes = (10_000, 200_000, 2_000_000, 8_000_000)
+    tabs = [datagen.skewed_table(n, seed=50 + i, device="cuda") for i, n in enumerate(sizes)]
+    return tabs, [esc.Table.from_datagen(t) for t in tabs]
+
+
+def test_served_results_equal_alone(esc):
+    from paper_1901_01488_gb300 import serve
+    tabs, etabs = _tables(esc)
+    work = datagen.batch_workload(400, seed=21, sizes=[t.nrows for t in tabs])
+    arr = serve.poisson_arrivals(len(work), 50_000, seed=3)
+    reqs = []
+    for j, ((ti, p), a) in enumerate(zip(work, arr)):
+        proj = datagen.SKEWED_PROJECTION if j % 4 == 0 else ()
+        cap = 0
+        if proj:
+            cap = esc.count(etabs[ti], esc.Predicate(etabs[ti], p.text)) + 1
+        reqs.append(serve.Request(j, ti, p.text, float(a), proj, cap))
+    srv = serve.Server(esc, etabs, mem_budget=256 << 20, max_batch=64, streams=2)
+    done = srv.run(reqs)
+    assert srv.waves > 1
+    assert srv.peak_bytes <= 256 << 20 or max(serve.request_bytes(etabs[r.table].nrows, r, srv.widths[r.table])
+                                               for r in reqs) > 256 << 20
+    for r in done:
+        p = esc.Predicate(etabs[r.table], r.text, tuple(r.proj))
+        if not r.proj:
+            assert r.count == esc.count(etabs[r.table], p), r.text
+        else:
+            n, ids, cols = esc.select(etabs[r.table], p)
+            assert r.count == n
+            assert torch.equal(r.rows[1][:n], ids)
+            for a, b in zip(r.rows[2], cols):
+                assert torch.equal(a[:n], b)
+    s = serve.latency_summary(done)
+    assert s["p50_ms"] > 0
+
+
+def test_admission_by_memory(esc):
+    from paper_1901_01488_gb300 import serve
+    tabs, etabs = _tables(esc)
+    work = datagen.batch_workload(120, seed=22, sizes=[t.nrows for t in tabs])
+    reqs = []
+    for j, (ti, p) in enumerate(work):
+        cap = esc.count(etabs[ti], esc.Predicate(etabs[ti], p.text)) + 1
+        reqs.append(serve.Request(j, ti, p.text, 0.0, datagen.SKEWED_PROJECTION, cap))
+    need = [serve.request_bytes(etabs[r.table].nrows, r, {"key": 4, "day": 4, "price": 8}) for r in reqs]
+    budget = max(max(need), 4 * int(np.median(need)))
+    srv = serve.Server(esc, etabs, mem_budget=budget, max_batch=1000, streams=2)
+    srv.run(reqs)
+    assert srv.peak_bytes <= budget
+    assert srv.waves >= 3          # the budget forced several waves

@@ -1,0 +1,127 @@
+"""The learned surrogate's kernels against the FP64 oracle, and its training
+and accuracy with exact ESC as the judge."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from paper_1901_01488_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def esc():
+    from paper_1901_01488_gb300 import build
+    build.build()
+    from paper_1901_01488_gb300 import esc as m
+    return m
+
+
+def _setup(esc, B, seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(esc.MLP_PARAMS, dtype=np.float32)
+    s = omlp.sizes()
+    o = 0
+    for k, shp in s.items():
+        n = int(np.prod(shp))
+        p[o:o + n] = rng.normal(0, 0.3 if k != "b3" else 0.1, n)
+        o += n
+    x = rng.random((B, 64)).astype(np.float32)
+    t = rng.normal(-3, 1, B).astype(np.float32)
+    params = torch.from_numpy(p).cuda()
+    wbf = params.to(torch.bfloat16).view(torch.int16).contiguous()
+    xb = torch.from_numpy(x).cuda().to(torch.bfloat16).view(torch.int16).contiguous()
+    # the oracle sees exactly what the device uses: bf16 weights and inputs, f32 biases
+    P = omlp.unflatten(p.astype(np.float64))
+    for k in ("W1", "W2", "w3"):
+        P[k] = omlp.round_bf16(P[k].astype(np.float32))
+    p_dev = omlp.flatten(P)
+    return params, wbf, xb, torch.from_numpy(t).cuda(), p_dev, omlp.round_bf16(x), t.astype(np.float64)
+
+
+def test_forward_matches_fp64(esc):
+    params, wbf, xb, t, p_dev, x64, _ = _setup(esc, 1001, 0)
+    y = torch.empty(1001, dtype=torch.float32, device="cuda")
+    esc.esc_mlp_forward(xb, wbf, params, y)
+    y_ref, _ = omlp.forward(p_dev, x64)
+    err = np.abs(y.cpu().numpy() - y_ref) / np.maximum(1.0, np.abs(y_ref))
+    assert err.max() < 1e-3, err.max()
+
+
+def test_gradient_matches_fp64(esc):
+    params, wbf, xb, t, p_dev, x64, t64 = _setup(esc, 777, 1)
+    grad = torch.zeros_like(params)
+    lsum = torch.zeros(1, dtype=torch.float32, device="cuda")
+    esc.esc_mlp_grad(xb, t, wbf, params, grad, lsum)
+    l_ref, g_ref = omlp.grad(p_dev, x64, t64)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(lsum.item() / 777 - l_ref) <= 1e-3 * abs(l_ref)
+    # each block of parameters within 1e-3 relative (to that block's largest gradient)
+    o = 0
+    for k, shp in omlp.sizes().items():
+        n = int(np.prod(shp))
+        scale = max(1e-6, np.abs(g_ref[o:o + n]).max())
+        assert np.abs(g[o:o + n] - g_ref[o:o + n]).max() <= 1e-3 * scale, k
+        o += n
+
+
+def test_adam_step(esc):
+    n = esc.MLP_PARAMS
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=n).astype(np.float32)
+    g = rng.normal(size=n).astype(np.float32)
+    params = torch.from_numpy(p0.copy()).cuda()
+    wbf = torch.zeros(n, dtype=torch.int16, device="cuda")
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    esc.esc_mlp_adam(params, wbf, torch.from_numpy(g).cuda(), m, v, 1e-3, 1)
+    # Adam's first step moves every parameter by lr * sign(g) (up to eps)
+    expect = p0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(params.cpu().numpy(), expect, rtol=1e-5, atol=1e-6)
+    assert torch.equal(wbf, params.to(torch.bfloat16).view(torch.int16))
+
+
+def test_training_and_qerror(esc):
+    from paper_1901_01488_gb300 import surrogate as S
+    t = datagen.skewed_table(2_000_000, seed=40, device="cuda")
+    table = esc.Table.from_datagen(t)
+    rng = np.random.default_rng(7)
+    n = 12_000
+    targets = 10.0 ** rng.uniform(-6, np.log10(0.9), n)
+    preds = [datagen.random_predicate(900_000 + j, float(targets[j])) for j in range(n)]
+    counts = S.exact_counts(esc, table, preds)
+    y = S.log_selectivity(counts, t.nrows)
+    X = S.encode_batch(preds)
+    ntr = int(0.9 * n)
+    model = S.Surrogate(esc, seed=3)
+    xb = S.to_bf16(X, "cuda")
+    yb = torch.from_numpy(y).cuda()
+    curve = model.fit(xb[:ntr], yb[:ntr], epochs=40, batch=2048, lr=3e-3)
+    assert curve[-1] < 0.25 * curve[0], curve
+    est = 10.0 ** model.predict(xb[ntr:]).cpu().numpy() * t.nrows
+    q = S.qerror(est, counts[ntr:])
+    h = S.Histograms({c.name: c.numpy()[:500_000] for c in t.columns})
+    ind = np.array([S.independence_estimate(h, p) for p in preds[ntr:]]) * t.nrows
+    qi = S.qerror(ind, counts[ntr:])
+    print(f"surrogate median q-error {np.median(q):.2f} p95 {np.percentile(q, 95):.1f}; "
+          f"independence median {np.median(qi):.2f} p95 {np.percentile(qi, 95):.1f}")
+    assert np.median(q) < 10.0
+
+
+def test_checkpoint_resume(esc, tmp_path):
+    from paper_1901_01488_gb300 import surrogate as S
+    rng = np.random.default_rng(5)
+    X = rng.random((4096, 64)).astype(np.float32)
+    y = (X[:, :8].sum(axis=1) - 4.0).astype(np.float32)
+    xb, yb = S.to_bf16(X, "cuda"), torch.from_numpy(y).cuda()
+    a = S.Surrogate(esc, seed=11)
+    a.fit(xb, yb, epochs=3, batch=512, lr=1e-3, seed=9)
+    torch.save(a.state_dict(), tmp_path / "ck.pt")
+    b = S.Surrogate(esc, seed=99)
+    b.load_state_dict(torch.load(tmp_path / "ck.pt"))
+    ca = a.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=10)
+    cb = b.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=10)
+    assert np.allclose(ca, cb, rtol=1e-3), (ca, cb)
