@@ -325,6 +325,13 @@ def run_batch(args):
     work = datagen.batch_workload(512, seed=3, sizes=sizes)
     proj = datagen.SKEWED_PROJECTION
     preds = [esc.Predicate(etabs[ti], p.text, proj) for ti, p in work]
+    # launch shape per (table size, read bytes per row) class from the autotuner
+    from paper_1901_01488_gb300.autotune import Autotuner
+    tuner = Autotuner(esc, repeats=2)
+    for ti, t in enumerate(etabs):
+        tuner.tune(t, [p for (tj, _), p in zip(work, preds) if tj == ti], materialise=True)
+    for (ti, _), p in zip(work, preds):
+        tuner.apply(etabs[ti], p, materialise=True)
     counts, _ = esc.esc_selectivity_batch([etabs[ti].handle for ti, _ in work], [p.handle for p in preds])
     rows_a = [p.alloc_rows(max(1, c), device=dev) for p, c in zip(preds, counts)]
     rows_b = [p.alloc_rows(max(1, c), device=dev) for p, c in zip(preds, counts)]
@@ -373,7 +380,9 @@ def run_batch(args):
            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))],
                           "what": "sub-query completion time after the batch starts (device clock)"},
            "one_launch_per_query": {"ms_per_batch": ms_single, "value": rows_total / (ms_single / 1e3)},
-           "bit_exact_vs_one_launch_per_query": same, "gpu_launches_per_batch": 3}
+           "bit_exact_vs_one_launch_per_query": same, "gpu_launches_per_batch": 3,
+           "autotuner": {"classes": len(tuner.cache),
+                         "choices (max_tile_rows, max_unit_kb, units_per_sm)": sorted(set(tuner.cache.values()))}}
     print(json.dumps(out), flush=True)
     esc.esc_batch_destroy(b)
 

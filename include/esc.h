@@ -118,6 +118,26 @@ esc_status esc_predicate_compile(const esc_table *table, const char *text,
                                  const char *const *proj, int32_t nproj, esc_pred **out);
 esc_status esc_predicate_destroy(esc_pred *pred);
 
+/* Launch shape of a compiled predicate's scans (the autotuner's knobs; not
+ * in the paper).  max_tile_rows: rows staged per tile (256..32768, a
+ * multiple of 256; the stage size caps it further); max_unit_kb: staged
+ * bytes per work unit (16..4096; a unit is claimed with one ticket and is the
+ * granularity of the compaction offsets); units_per_sm: work units to aim
+ * for per SM (1..64; more balances load, fewer amortises per-unit work).
+ * Defaults: 32768, 512, 8.  Results never depend on these. */
+typedef struct esc_tuning {
+    uint32_t max_tile_rows;
+    uint32_t max_unit_kb;
+    int32_t units_per_sm;
+    int32_t reserved;
+} esc_tuning;
+
+/* Sets (tuning NULL: restores the defaults) or reads a predicate's launch
+ * shape.  ESC_EINVAL for values outside the ranges above.  Not thread-safe
+ * against concurrent calls that use the same predicate. */
+esc_status esc_predicate_set_tuning(esc_pred *pred, const esc_tuning *tuning);
+esc_status esc_predicate_get_tuning(const esc_pred *pred, esc_tuning *out);
+
 /* Writes a NUL-terminated listing of the compiled program (read columns,
  * projection, one line per instruction) into buf[0..buflen).  ESC_EINVAL if
  * it does not fit. */

@@ -758,6 +758,30 @@ esc_status esc_predicate_compile(const esc_table *t, const char *text, const cha
   return ESC_OK;
 }
 
+esc_status esc_predicate_set_tuning(esc_pred *p, const esc_tuning *t) {
+  if (!p) return fail(ESC_EINVAL, "esc_predicate_set_tuning: pred is NULL");
+  if (!t) {
+    p->tuning = kDefaultTuning;
+    return ESC_OK;
+  }
+  if (t->max_tile_rows < 256 || t->max_tile_rows > 32768 || t->max_tile_rows % 256 != 0)
+    return fail(ESC_EINVAL, "esc_predicate_set_tuning: max_tile_rows must be a multiple of 256 in 256..32768");
+  if (t->max_unit_kb < 16 || t->max_unit_kb > 4096)
+    return fail(ESC_EINVAL, "esc_predicate_set_tuning: max_unit_kb must be in 16..4096");
+  if (t->units_per_sm < 1 || t->units_per_sm > 64)
+    return fail(ESC_EINVAL, "esc_predicate_set_tuning: units_per_sm must be in 1..64");
+  p->tuning = *t;
+  p->tuning.reserved = 0;
+  clear_error();
+  return ESC_OK;
+}
+
+esc_status esc_predicate_get_tuning(const esc_pred *p, esc_tuning *out) {
+  if (!p || !out) return fail(ESC_EINVAL, "esc_predicate_get_tuning: NULL argument");
+  *out = p->tuning;
+  return ESC_OK;
+}
+
 esc_status esc_predicate_destroy(esc_pred *p) {
   delete p;
   return ESC_OK;

@@ -130,6 +130,7 @@ struct esc_table {
 
 struct esc_pred {
   const esc_table *table;
+  esc_tuning tuning{32768u, 512u, 8, 0};
   std::string text;
   int32_t ninstr = 0;
   std::vector<int32_t> ref_cols;    // table column index of each stage slot
@@ -144,6 +145,8 @@ namespace esc {
 int dtype_width(int32_t dt);
 esc_status fail(esc_status s, const std::string &msg);
 void clear_error();
+// Defaults of esc_tuning.
+constexpr esc_tuning kDefaultTuning{32768u, 512u, 8, 0};
 // Fills the static part of a Query (program, read columns, projection) for a pred.
 void fill_query_program(const esc_pred *p, Query *q);
 // Granlund-Montgomery unsigned magic for divisor d (Fig. 4.1 of their paper).

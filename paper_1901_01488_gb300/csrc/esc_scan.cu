@@ -1137,13 +1137,13 @@ esc_status device_state(DeviceState **out) {
 
 // Tile size for a query: as many rows as fit in one stage, a multiple of the
 // 256-row group, at most kMaxTileRows.
-uint32_t tile_rows_for(const Query &q) {
+uint32_t tile_rows_for(const Query &q, const esc_tuning &tu) {
   uint32_t bpr = 0;
   for (int i = 0; i < q.nref; ++i) bpr += q.ref_w[i];
   if (bpr == 0) bpr = 1;
   uint32_t t = (kStageBytes / bpr / kGroup) * kGroup;
   t = std::max<uint32_t>(t, kGroup);
-  return std::min<uint32_t>(t, kMaxTileRows);
+  return std::min<uint32_t>(std::min<uint32_t>(t, kMaxTileRows), tu.max_tile_rows);
 }
 
 // Stage layout (read columns back to back, each slice 128-byte aligned), and
@@ -1152,8 +1152,8 @@ uint32_t tile_rows_for(const Query &q) {
 // staged columns and there are >= 8 per SM when the table is large enough,
 // which keeps the unit rate (look-backs per microsecond) low enough for the
 // look-back chain to keep up with HBM.
-void layout_stage(Query &q, int sms) {
-  q.tile_rows = tile_rows_for(q);
+void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
+  q.tile_rows = tile_rows_for(q, tu);
   uint32_t off = 0, bpr = 0;
   for (int i = 0; i < q.nref; ++i) {
     q.stage_off[i] = off;
@@ -1170,8 +1170,8 @@ void layout_stage(Query &q, int sms) {
   q.ngroups = (q.nrows + kGroup - 1) / kGroup;
   const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);
   const uint32_t max_ut = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>((512ull * 1024) / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
-  const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * 8);
+      1, std::min<uint64_t>((uint64_t)tu.max_unit_kb * 1024 / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
+  const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * tu.units_per_sm);
   q.unit_tiles = std::min(std::max<uint32_t>(want, 1), max_ut);
   q.nunits = (q.ntiles + q.unit_tiles - 1) / q.unit_tiles;
 }
@@ -1252,7 +1252,7 @@ esc_status prepare_query(const esc_table *t, const esc_pred *p, const esc_rows *
       if (rows->capacity && !q->out_proj[i]) return fail(ESC_EINVAL, "a projected output pointer is NULL");
     }
   }
-  layout_stage(*q, d->sms);
+  layout_stage(*q, d->sms, p->tuning);
   return ESC_OK;
 }
 
@@ -1765,7 +1765,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
         return fail(ESC_EINVAL, "esc_selectivity_noalloc: a projected output pointer is NULL");
     }
   }
-  layout_stage(q, d->sms);
+  layout_stage(q, d->sms, p->tuning);
   L.nq = 1;
   L.total_units = q.nunits;
   const size_t head = (sizeof(NoAllocHead) + 255) & ~(size_t)255;

@@ -33,6 +33,11 @@ class esc_column(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p)]
 
 
+class esc_tuning(ctypes.Structure):
+    _fields_ = [("max_tile_rows", ctypes.c_uint32), ("max_unit_kb", ctypes.c_uint32),
+                ("units_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class esc_rows(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_uint64), ("row_ids", ctypes.c_void_p),
                 ("proj", ctypes.POINTER(ctypes.c_void_p)), ("written", ctypes.c_uint64)]
@@ -48,6 +53,8 @@ _sig = {
                                ctypes.POINTER(_P)], _S),
     "esc_predicate_destroy": ([_P], _S),
     "esc_predicate_explain": ([_P, ctypes.c_char_p, ctypes.c_uint64], _S),
+    "esc_predicate_set_tuning": ([_P, ctypes.POINTER(esc_tuning)], _S),
+    "esc_predicate_get_tuning": ([_P, ctypes.POINTER(esc_tuning)], _S),
     "esc_selectivity": ([_P, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(esc_rows), _P], _S),
     "esc_selectivity_async": ([_P, _P, _P, ctypes.POINTER(esc_rows), _P], _S),
     "esc_selectivity_noalloc": ([_P, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(esc_rows), _P], _S),
@@ -132,6 +139,21 @@ def esc_predicate_explain(pred: int) -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     _check(_lib.esc_predicate_explain(pred, buf, len(buf)), "esc_predicate_explain")
     return buf.value.decode()
+
+
+def esc_predicate_set_tuning(pred: int, tuning: Optional[Tuple[int, int, int]]) -> None:
+    """tuning = (max_tile_rows, max_unit_kb, units_per_sm) or None for the defaults."""
+    if tuning is None:
+        _check(_lib.esc_predicate_set_tuning(pred, None), "esc_predicate_set_tuning")
+        return
+    t = esc_tuning(tuning[0], tuning[1], tuning[2], 0)
+    _check(_lib.esc_predicate_set_tuning(pred, ctypes.byref(t)), "esc_predicate_set_tuning")
+
+
+def esc_predicate_get_tuning(pred: int) -> Tuple[int, int, int]:
+    t = esc_tuning()
+    _check(_lib.esc_predicate_get_tuning(pred, ctypes.byref(t)), "esc_predicate_get_tuning")
+    return t.max_tile_rows, t.max_unit_kb, t.units_per_sm
 
 
 def _rows_struct(capacity: int, row_ids: Optional[torch.Tensor], proj: Sequence[torch.Tensor]):
