@@ -383,6 +383,145 @@ struct Lowerer {
     return leaf;
   }
 
+  bool udf_unsigned(int col, int col2) const {
+    auto u = [&](int c) { return t->dtypes[c] == ESC_U8 || t->dtypes[c] == ESC_U16; };
+    return u(col) && u(col2);
+  }
+
+  // Value domain of a leaf's operand.
+  void domain(const Low &l, int64_t *dlo, int64_t *dhi) const {
+    if (l.leaf.op == OP_UDF) {
+      *dhi = l.m - 1;
+      *dlo = udf_unsigned(l.col, l.col2) ? 0 : -(l.m - 1);
+    } else {
+      dtype_domain(t->dtypes[l.col], dlo, dhi);
+    }
+  }
+
+  // Key of a leaf's operand: a column, or udf(a, b, m) with {a, b} unordered
+  // (the wrapped product commutes).  Empty for anything else.
+  static std::string operand_key(const Low &l) {
+    if (l.kind != Low::LEAF) return std::string();
+    if (l.leaf.op == OP_UDF)
+      return "u" + std::to_string(std::min(l.col, l.col2)) + "," + std::to_string(std::max(l.col, l.col2)) + "," +
+             std::to_string(l.m);
+    return "c" + std::to_string(l.col);
+  }
+
+  // Tests on the same operand among the children of one AND (is_and) or OR
+  // combine into at most one range and one IN list for that operand:
+  //  * AND: ranges intersect; IN lists intersect and keep only values inside
+  //    the range, which the list then replaces; an empty result makes the
+  //    whole AND false (returns false);
+  //  * OR: overlapping or adjacent ranges unite; IN lists unite and lose the
+  //    values some range already holds; a range covering the operand's
+  //    domain makes the whole OR true (returns false).
+  // Exact set algebra on integers, so results never change.
+  bool merge_same_operand(std::vector<Low> &kids, bool is_and) {
+    std::vector<Low> out;
+    std::vector<std::string> keys;
+    std::vector<std::vector<size_t>> groups;
+    for (size_t i = 0; i < kids.size(); ++i) {
+      const std::string k = operand_key(kids[i]);
+      size_t g = keys.size();
+      if (!k.empty())
+        for (size_t j = 0; j < keys.size(); ++j)
+          if (keys[j] == k) g = j;
+      if (g == keys.size()) {
+        keys.push_back(k);
+        groups.emplace_back();
+      }
+      groups[g].push_back(i);
+    }
+    for (size_t g = 0; g < groups.size(); ++g) {
+      if (keys[g].empty() || groups[g].size() == 1) {
+        for (size_t i : groups[g]) out.push_back(std::move(kids[i]));
+        continue;
+      }
+      const Low &proto = kids[groups[g][0]];
+      int64_t dlo, dhi;
+      domain(proto, &dlo, &dhi);
+      std::vector<std::pair<int64_t, int64_t>> ranges;
+      std::vector<std::set<int64_t>> lists;
+      for (size_t i : groups[g]) {
+        const Low &l = kids[i];
+        if (l.leaf.op == OP_IN) lists.emplace_back(l.vals.begin(), l.vals.end());
+        else ranges.push_back({l.leaf.lo, l.leaf.hi});
+      }
+      std::vector<std::pair<int64_t, int64_t>> rs;
+      std::set<int64_t> vals;
+      bool have_list = !lists.empty();
+      if (is_and) {
+        if (!ranges.empty()) {
+          int64_t lo = INT64_MIN, hi = INT64_MAX;
+          for (auto &r : ranges) {
+            lo = std::max(lo, r.first);
+            hi = std::min(hi, r.second);
+          }
+          if (lo > hi) return false;
+          rs.push_back({lo, hi});
+        }
+        if (have_list) {
+          vals = lists[0];
+          for (size_t k = 1; k < lists.size(); ++k) {
+            std::set<int64_t> both;
+            for (int64_t v : vals)
+              if (lists[k].count(v)) both.insert(v);
+            vals.swap(both);
+          }
+          if (!rs.empty()) {
+            std::set<int64_t> in;
+            for (int64_t v : vals)
+              if (v >= rs[0].first && v <= rs[0].second) in.insert(v);
+            vals.swap(in);
+            rs.clear();  // every value left is inside the range
+          }
+          if (vals.empty()) return false;
+        }
+      } else {
+        std::sort(ranges.begin(), ranges.end());
+        for (auto &r : ranges) {
+          if (!rs.empty() && (rs.back().second == INT64_MAX || rs.back().second + 1 >= r.first))
+            rs.back().second = std::max(rs.back().second, r.second);
+          else
+            rs.push_back(r);
+        }
+        for (auto &r : rs)
+          if (r.first <= dlo && r.second >= dhi) return false;
+        for (auto &l : lists)
+          for (int64_t v : l) {
+            bool held = false;
+            for (auto &r : rs) held = held || (v >= r.first && v <= r.second);
+            if (!held) vals.insert(v);
+          }
+        have_list = !vals.empty();
+      }
+      for (auto &r : rs) {
+        Low leaf = proto;
+        leaf.vals.clear();
+        leaf.leaf.op = proto.leaf.op == OP_UDF ? OP_UDF : OP_RANGE;
+        leaf.leaf.lo = r.first;
+        leaf.leaf.hi = r.second;
+        out.push_back(std::move(leaf));
+      }
+      if (have_list) {
+        Low leaf = proto;
+        if (vals.size() == 1) {
+          leaf.vals.clear();
+          leaf.leaf.op = OP_RANGE;
+          leaf.leaf.lo = leaf.leaf.hi = *vals.begin();
+        } else {
+          leaf.leaf.op = OP_IN;
+          leaf.leaf.lo = leaf.leaf.hi = 0;
+          leaf.vals.assign(vals.begin(), vals.end());
+        }
+        out.push_back(std::move(leaf));
+      }
+    }
+    kids = std::move(out);
+    return true;
+  }
+
   Low lower(const Ast &a) {
     switch (a.kind) {
       case Ast::CONST: return mk(a.value ? Low::TRUE_ : Low::FALSE_);
@@ -448,6 +587,8 @@ struct Lowerer {
             n.kids.push_back(std::move(c));
           }
         }
+        // tests on one operand combine: AND intersects, OR unites
+        if (!merge_same_operand(n.kids, is_and)) return mk(is_and ? Low::FALSE_ : Low::TRUE_);
         if (n.kids.empty()) return mk(is_and ? Low::TRUE_ : Low::FALSE_);
         if (n.kids.size() == 1) return std::move(n.kids[0]);
         return n;
@@ -582,6 +723,11 @@ struct Emitter {
           pool((int64_t)mult);
           pool((int64_t)s1);
           pool((int64_t)s2);
+          // moduli below 2^16: ceil(2^64 / m) for Lemire, Kaser & Kurz's direct
+          // 32-bit remainder (Softw. Pract. Exper. 2019), and 2^32 mod m
+          const uint64_t um = (uint64_t)l.m;
+          pool(um < 65536 ? (int64_t)(~0ull / um + 1) : 0);
+          pool(um < 65536 ? (int64_t)((1ull << 32) % um) : 0);
         } else if (ins.op == OP_IN) {
           ins.n = (uint16_t)l.vals.size();
           bool small = true;

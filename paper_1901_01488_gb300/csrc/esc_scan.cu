@@ -246,6 +246,29 @@ __device__ __forceinline__ int64_t udf_rem(int64_t a, int64_t b, uint64_t d, uin
   return p < 0 ? -r : r;
 }
 
+// x mod d for 32-bit x and 1 <= d < 2^32, with M = ceil(2^64 / d): the low 64
+// bits of M * x, times d, high 64 bits (Lemire, Kaser & Kurz 2019, direct
+// remainder; exact for every 32-bit x and d).
+__device__ __forceinline__ uint32_t fastmod32(uint32_t x, uint64_t M, uint32_t d) {
+  const uint64_t low = M * (uint64_t)x;
+  const uint64_t u = (uint64_t)(uint32_t)(low >> 32) * d + __umulhi((uint32_t)low, d);
+  return (uint32_t)(u >> 32);
+}
+
+// udf_rem for moduli d < 2^16: |p| = H 2^32 + L gives
+// |p| mod d = ((H mod d) (2^32 mod d) + L mod d) mod d, where the inner sum
+// stays below d^2 < 2^32; K = 2^32 mod d.
+__device__ __forceinline__ int32_t udf_rem_small(int64_t a, int64_t b, uint32_t d, uint64_t M, uint32_t K) {
+  const uint64_t p = (uint64_t)a * (uint64_t)b;
+  const uint32_t s = (uint32_t)((int64_t)p >> 63);  // 0 or all ones
+  const uint64_t s64 = (uint64_t)(int64_t)(int32_t)s;
+  const uint64_t n = (p ^ s64) - s64;               // |p|, 2^63 included
+  const uint32_t r1 = fastmod32((uint32_t)(n >> 32), M, d);
+  const uint32_t r2 = fastmod32((uint32_t)n, M, d);
+  const uint32_t r = fastmod32(r1 * K + r2, M, d);
+  return (int32_t)((r ^ s) - s);
+}
+
 // ------------------------------------------------------------------ evaluation
 // Runs the program on this lane's 8 rows of NG groups of the staged tile at
 // once (one decode per instruction for all of them, NG independent chains).
@@ -367,18 +390,37 @@ __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage
         const int w2 = width_of(dt2);
         const uint8_t *col2 = stage + (h.w & 0xffffu);
         const int64_t *P = &Q->pool[h.z & 0xffffu];
-        const uint64_t d = (uint64_t)P[0], mult = (uint64_t)P[1];
-        const int sh1 = (int)P[2], sh2 = (int)P[3];
-        const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
+        const uint64_t d = (uint64_t)P[0];
+        if (d < 65536u) {
+          // remainder and range in 32 bits (the range lies inside (-d, d))
+          const uint64_t M = (uint64_t)P[4];
+          const uint32_t K = (uint32_t)P[5], d32 = (uint32_t)d;
+          const uint32_t lo = (uint32_t)lh.x, span = (uint32_t)((uint64_t)lh.y - (uint64_t)lh.x);
 #pragma unroll
-        for (int i = 0; i < NG; ++i) {
-          int64_t a[8], b[8];
-          load8(dt, col + (size_t)grp[i] * kGroup * w, lane, a);
-          load8(dt2, col2 + (size_t)grp[i] * kGroup * w2, lane, b);
+          for (int i = 0; i < NG; ++i) {
+            int64_t a[8], b[8];
+            load8(dt, col + (size_t)grp[i] * kGroup * w, lane, a);
+            load8(dt2, col2 + (size_t)grp[i] * kGroup * w2, lane, b);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
-            m[i] |= (uint32_t)((uint64_t)r - (uint64_t)lh.x <= span) << k;
+            for (int k = 0; k < 8; ++k) {
+              const int32_t r = udf_rem_small(a[k], b[k], d32, M, K);
+              m[i] |= (uint32_t)((uint32_t)r - lo <= span) << k;
+            }
+          }
+        } else {
+          const uint64_t mult = (uint64_t)P[1];
+          const int sh1 = (int)P[2], sh2 = (int)P[3];
+          const uint64_t span = (uint64_t)lh.y - (uint64_t)lh.x;
+#pragma unroll
+          for (int i = 0; i < NG; ++i) {
+            int64_t a[8], b[8];
+            load8(dt, col + (size_t)grp[i] * kGroup * w, lane, a);
+            load8(dt2, col2 + (size_t)grp[i] * kGroup * w2, lane, b);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int64_t r = udf_rem(a[k], b[k], d, mult, sh1, sh2);
+              m[i] |= (uint32_t)((uint64_t)r - (uint64_t)lh.x <= span) << k;
+            }
           }
         }
       }
@@ -640,6 +682,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
             const uint32_t c = __popc(m);
             acc += c;
             uacc += c;
+            const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
+            if (gc) {
+              const uint32_t gcount = __reduce_add_sync(FULL, c);
+              if (lane == 0) gc[gidx] = gcount;
+              if (gcount == 0) continue;  // the write pass reads no bitmap word of an empty group
+            }
             uint32_t word = 0;
 #pragma unroll
             for (int p = 0; p < 8; ++p) {  // words of rows 32p .. 32p+31 of the group
@@ -648,13 +696,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
               const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
               if (lane == p) word = bb;
             }
-            const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
             const uint32_t wi = gidx * 8u + (uint32_t)lane;
             if (lane < 8 && wi < nwords) bm[wi] = word;
-            if (gc) {
-              const uint32_t gcount = __reduce_add_sync(FULL, c);
-              if (lane == 0) gc[gidx] = gcount;
-            }
           }
         }
       }

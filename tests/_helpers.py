@@ -40,7 +40,7 @@ def random_preds(count=400, seed=17):
     def opd():
         if rng.random() < 0.2:
             x, y = rng.choice(names, 2)
-            return f"udf({x}, {y}, {int(rng.choice([1, 2, 7, 97, 1000003, 2**62 + 1]))})"
+            return f"udf({x}, {y}, {int(rng.choice([1, 2, 7, 97, 65535, 65536, 1000003, 2**62 + 1]))})"
         return str(rng.choice(names))
 
     def atom():

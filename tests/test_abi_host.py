@@ -95,6 +95,70 @@ def test_compiled_program_means_the_predicate(esc):
     assert checked > 300
 
 
+def _same_operand_preds(count, seed):
+    """Conjunctions and disjunctions of several tests on the same few operands
+    (ranges, points, IN lists, udf both ways round), so that the compiler's
+    merging of tests on one operand is exercised against the oracle."""
+    rng = np.random.default_rng(seed)
+    opds = ["a", "b", "udf(a, b, 7)", "udf(b, a, 7)", "udf(c, e, 97)", "udf(e, c, 97)"]
+
+    def atom(o):
+        k = rng.integers(5)
+        v = int(rng.integers(-60, 60)) if o != "b" else int(rng.integers(-5, 260))
+        if k == 0:
+            return f"{o} {rng.choice(['=', '<', '<=', '>', '>='])} {v}"
+        if k == 1:
+            return f"{o} BETWEEN {v} AND {v + int(rng.integers(-3, 40))}"
+        if k == 2:
+            vals = ", ".join(str(v + int(rng.integers(-8, 8))) for _ in range(int(rng.integers(1, 6))))
+            return f"{o} IN ({vals})"
+        if k == 3:
+            return f"{o} != {v}"
+        return f"NOT ({o} BETWEEN {v} AND {v + 5})"
+
+    out = []
+    for _ in range(count):
+        o = rng.choice(opds[:2] if rng.random() < 0.5 else opds)
+        parts = [atom(o if rng.random() < 0.8 else rng.choice(opds)) for _ in range(int(rng.integers(2, 6)))]
+        j = " AND " if rng.random() < 0.5 else " OR "
+        inner = j.join(parts)
+        out.append(inner if rng.random() < 0.7 else f"({inner}) {'OR' if j == ' AND ' else 'AND'} {atom(o)}")
+    return out
+
+
+def test_merged_tests_keep_the_meaning(esc):
+    cols = host_table()
+    t = _table(esc, cols)
+    for text in _same_operand_preds(300, 5):
+        got = _interpret(esc.Predicate(t, text).explain(), cols)
+        ids, _ = oracle.select(text, cols)
+        assert np.array_equal(np.flatnonzero(got), ids.astype(np.int64)), text
+
+
+def test_tests_on_one_operand_merge(esc):
+    t = _table(esc, host_table(100))
+
+    def instrs(text):
+        return [l.split(None, 2)[2] for l in esc.Predicate(t, text).explain().splitlines() if l.startswith("instr")]
+
+    # AND intersects (udf operands in either order), OR unites adjacent ranges
+    assert instrs("udf(c, a, 97) > 16 AND udf(a, c, 97) > 94") == ["UDF 0 i64 1 i32 97 95 96"]
+    assert instrs("e = 3 AND e = 3") == ["RANGE 0 i32 3 3"]
+    assert instrs("a BETWEEN 1 AND 5 OR a BETWEEN 6 AND 9 OR a = 20") == [
+        "RANGE 0 i32 1 9", "RANGE 0 i32 20 20", "OR"]
+    assert instrs("b IN (1, 4, 6) AND b BETWEEN 2 AND 9") == ["IN 0 u8 4,6"]
+    assert instrs("a IN (1, 2, 3) OR a IN (3, 4)") == ["IN 0 i32 1,2,3,4"]
+    assert instrs("a IN (1, 2, 30) OR a BETWEEN 0 AND 10") == ["RANGE 0 i32 0 10", "RANGE 0 i32 30 30", "OR"]
+    # empty conjunction, covering disjunction
+    assert instrs("b = 1 AND b IN (4, 6)") == ["FALSE"]
+    assert instrs("a = 2 AND (b = 1 AND b = 3)") == ["FALSE"]
+    assert instrs("b < 100 OR b >= 50") == ["TRUE"]
+    assert instrs("udf(b, d, 5) <= 2 OR udf(d, b, 5) > 1") == ["TRUE"]
+    # different operands, or different moduli, stay apart
+    assert [i.split()[0] for i in instrs("udf(c, a, 97) > 16 AND udf(c, a, 89) > 16")].count("UDF") == 2
+    assert len(instrs("a = 1 AND e = 1")) == 3
+
+
 def test_compile_errors(esc):
     cols = host_table(100)
     t = _table(esc, cols)
