@@ -84,12 +84,12 @@ struct Query {
   uint32_t nunits;
   uint32_t unit_base;     // first global ticket of this query
   uint32_t gmax;          // groups per full tile (tile_rows / kGroup)
-  uint32_t wunit_base;    // first block of this query in the offsets kernel (compaction only)
+  uint32_t wunit_base;    // first block of this query in the write kernel (compaction only)
   uint32_t stage_off[kMaxRef];    // byte offset of each read column in a stage
   uint8_t ref_w[kMaxRef];         // element width of each read column
   uint8_t proj_w[kMaxProj];
   int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
-  uint32_t gblock_base;   // first block of this query in the gather kernel (compaction only)
+  uint32_t pad0;
   uint32_t ngroups;       // 256-row groups: ceil(nrows / 256)
   uint32_t pad1[2];
   const uint8_t *ref_ptr[kMaxRef];
@@ -100,7 +100,7 @@ struct Query {
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
   uint32_t *gcounts;              // MODE_SELECT: qualifying rows per 256-row group (scratch)
-  unsigned long long *goff;       // compaction: first output slot of each group (scratch)
+  void *pad2;
   unsigned long long *unit_total; // MODE_SELECT: qualifying rows per unit (zeroed)
   unsigned long long *unit_status;// write kernel's decoupled look-back words, one per unit (zeroed)
   unsigned int *tiles_left;       // completion countdown (set before launch; see the kernels)

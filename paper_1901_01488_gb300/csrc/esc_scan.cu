@@ -255,18 +255,38 @@ __device__ __forceinline__ uint32_t fastmod32(uint32_t x, uint64_t M, uint32_t d
   return (uint32_t)(u >> 32);
 }
 
-// udf_rem for moduli d < 2^16: |p| = H 2^32 + L gives
-// |p| mod d = ((H mod d) (2^32 mod d) + L mod d) mod d, where the inner sum
-// stays below d^2 < 2^32; K = 2^32 mod d.
-__device__ __forceinline__ int32_t udf_rem_small(int64_t a, int64_t b, uint32_t d, uint64_t M, uint32_t K) {
-  const uint64_t p = (uint64_t)a * (uint64_t)b;
-  const uint32_t s = (uint32_t)((int64_t)p >> 63);  // 0 or all ones
-  const uint64_t s64 = (uint64_t)(int64_t)(int32_t)s;
-  const uint64_t n = (p ^ s64) - s64;               // |p|, 2^63 included
-  const uint32_t r1 = fastmod32((uint32_t)(n >> 32), M, d);
-  const uint32_t r2 = fastmod32((uint32_t)n, M, d);
-  const uint32_t r = fastmod32(r1 * K + r2, M, d);
-  return (int32_t)((r ^ s) - s);
+// Remainders of 8 udf products for a modulus d < 2^16, as 32-bit signed
+// values (truncated: the sign of the product).  With |p| = H 2^32 + L,
+// |p| mod d = ((H mod d) (2^32 mod d) + L mod d) mod d, the inner sum staying
+// below d^2 < 2^32 (K = 2^32 mod d); when every |p| of the warp's rows is
+// below 2^32 (H = 0), one remainder per row suffices.
+__device__ __forceinline__ void udf_rem_small8(const int64_t (&a)[8], const int64_t (&b)[8], uint32_t d, uint64_t M,
+                                               uint32_t K, int32_t (&r)[8]) {
+  uint64_t n[8];
+  uint32_t s[8], hi = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint64_t p = (uint64_t)a[k] * (uint64_t)b[k];
+    s[k] = (uint32_t)((int64_t)p >> 63);  // 0 or all ones
+    const uint64_t s64 = (uint64_t)(int64_t)(int32_t)s[k];
+    n[k] = (p ^ s64) - s64;               // |p|, 2^63 included
+    hi |= (uint32_t)(n[k] >> 32);
+  }
+  if (__any_sync(FULL, hi != 0)) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t r1 = fastmod32((uint32_t)(n[k] >> 32), M, d);
+      const uint32_t r2 = fastmod32((uint32_t)n[k], M, d);
+      const uint32_t x = fastmod32(r1 * K + r2, M, d);
+      r[k] = (int32_t)((x ^ s[k]) - s[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t x = fastmod32((uint32_t)n[k], M, d);
+      r[k] = (int32_t)((x ^ s[k]) - s[k]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -401,11 +421,10 @@ __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage
             int64_t a[8], b[8];
             load8(dt, col + (size_t)grp[i] * kGroup * w, lane, a);
             load8(dt2, col2 + (size_t)grp[i] * kGroup * w2, lane, b);
+            int32_t r[8];
+            udf_rem_small8(a, b, d32, M, K, r);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int32_t r = udf_rem_small(a[k], b[k], d32, M, K);
-              m[i] |= (uint32_t)((uint32_t)r - lo <= span) << k;
-            }
+            for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)((uint32_t)r[k] - lo <= span) << k;
           }
         } else {
           const uint64_t mult = (uint64_t)P[1];
@@ -500,7 +519,8 @@ struct SmemLayout {
   static constexpr size_t bars = qslot + (size_t)kStages * sizeof(Query);  // full[S] empty[S]
   static constexpr size_t meta = bars + 2 * kStages * 8;
   static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);      // [S] int32
-  static constexpr size_t total = slotq + kStages * 4;
+  static constexpr size_t take = slotq + kStages * 4;                       // [S] u32 pair claims
+  static constexpr size_t total = take + kStages * 4;
 };
 
 // ------------------------------------------------------------------ the scan kernel
@@ -514,6 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   uint64_t *empty_bar = full_bar + kStages;
   StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SmemLayout::meta);
   int32_t *slotq = reinterpret_cast<int32_t *>(smem + SmemLayout::slotq);
+  uint32_t *take = reinterpret_cast<uint32_t *>(smem + SmemLayout::take);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -600,6 +621,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
         __syncwarp();
         if (lane == 0) {
           StageMeta &m = meta[s];
+          take[s] = 0;  // every consumer has left the stage (empty barrier)
           m.q = qc;
           m.tile = tile;
           m.rows = rows;
@@ -619,7 +641,6 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   }
 
   // ---------------------------------------------------------------- consumers
-  const int cw = warp - 1;
   int s = 0;
   uint32_t phase = 0;
   // Running sums flushed with one atomic when the query / unit changes.
@@ -656,10 +677,20 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
     acc_q = mt.q;
     acc_ptr = Q->count;
     uacc_ptr = uptr;
+    // Consumers claim pairs of adjacent groups of the stage from a shared
+    // counter until none is left, then move on to the next stage: the work of
+    // a stage spreads over every consumer whatever its group count, and a warp
+    // that finishes early starts on the next stage.
+    const int npairs = (ngroups + 1) >> 1;
+    auto claim = [&]() {
+      int j = 0;
+      if (lane == 0) j = (int)atomicAdd(&take[s], 1u);
+      return __shfl_sync(FULL, j, 0);
+    };
     if (mt.dead == 0) {
       if (mode == MODE_COUNT) {
-        for (int g = cw; g < ngroups; g += 2 * kConsumers) {
-          const int g1 = g + kConsumers;
+        for (int j = claim(); j < npairs; j = claim()) {
+          const int g = 2 * j, g1 = g + 1;
           const int gs[2] = {g, g1 < ngroups ? g1 : g};
           uint32_t m[2];
           eval_groups<2>(Q, stage, gs, lane, m);
@@ -670,8 +701,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
         const uint32_t nwords = (Q->nrows + 31u) / 32u;
         uint32_t *bm = Q->bitmap;
         uint32_t *gc = mode == MODE_SELECT ? Q->gcounts : nullptr;
-        for (int g = cw; g < ngroups; g += 2 * kConsumers) {
-          const int g1 = g + kConsumers;
+        for (int j = claim(); j < npairs; j = claim()) {
+          const int g = 2 * j, g1 = g + 1;
           const int gs[2] = {g, g1 < ngroups ? g1 : g};
           uint32_t mm[2];
           eval_groups<2>(Q, stage, gs, lane, mm);
@@ -712,42 +743,27 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   }
 }
 
-// ------------------------------------------------------------------ the write kernels
-// Second pass of ordered compaction, in two launches.
-//
-// offsets_kernel: one block per work unit (<= 65536 rows, <= 256 groups of
-// 256 rows).  The unit's output offset comes from a decoupled look-back over
-// the units before it (Merrill & Garland 2016): every unit's aggregate is
-// already final (written by the scan kernel), so the look-back adds
-// aggregates until it meets a unit whose inclusive prefix another block has
-// published, and never waits.  A block-wide scan of the group counts then
-// gives every group's first output slot.
-//
-// gather_kernel: 8 groups per warp, independent of one another.  Dense full
-// groups are read with 16-byte vector loads (lane l: rows 8l .. 8l+7),
-// staged in shared memory at their output slots and stored with lane =
-// output slot; in other groups the j-th qualifying row goes to lane j % 32
-// and is copied directly.
+// ------------------------------------------------------------------ the write kernel
+// Second pass of ordered compaction, one block per work unit (<= 65536 rows,
+// <= 256 groups of 256 rows: one thread per group).
+//  1. The unit's first output slot: a decoupled look-back over the units
+//     before it (Merrill & Garland 2016).  Every unit's aggregate is already
+//     final (written by the scan kernel), so the look-back adds aggregates
+//     until it meets a unit whose inclusive prefix another block published,
+//     and never waits.
+//  2. Each group's first slot: a block-wide exclusive scan of the group
+//     counts of the unit.
+//  3. Warp w writes groups 32w .. 32w+31 of the unit.  A dense group (at least
+//     kDenseMin qualifying rows, all 256 rows inside the table) takes the
+//     whole warp: 16-byte vector loads of the projected columns (lane l: rows
+//     8l .. 8l+7), staged in shared memory at their output slots, stored with
+//     lane = slot.  Every other group takes one lane, which walks its group's
+//     bitmap words in row order and stages (row, slot) entries; the warp then
+//     copies the staged entries, 4 per lane, loads before stores.
 
-constexpr int kOffsetThreads = 256;   // one thread per group of a unit
-constexpr int kGatherThreads = 256;
-constexpr int kGatherGroupsPerWarp = 8;
-constexpr int kGatherGroups = (kGatherThreads / 32) * kGatherGroupsPerWarp;  // 64 per block
-
-// Position of the r-th set bit (0-based) of x; r < popc(x).
-__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t r) {
-  uint32_t pos = 0;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const uint32_t c = __popc(x & ((1u << w) - 1u));
-    if (r >= c) {
-      r -= c;
-      x >>= w;
-      pos += w;
-    }
-  }
-  return pos;
-}
+constexpr int kWriteThreads = 256;
+constexpr uint32_t kDenseMin = 97;
+constexpr uint32_t kStageEntries = 512;  // sparse entries staged per warp (2 KB)
 
 __device__ __forceinline__ uint64_t load_elem(const uint8_t *base, uint32_t row, int w) {
   switch (w) {
@@ -827,8 +843,115 @@ __device__ __forceinline__ int block_query(const Launch &L, F base) {
   return lo;
 }
 
-__global__ void __launch_bounds__(kOffsetThreads) offsets_kernel(const __grid_constant__ Launch L) {
-  __shared__ uint32_t wsum[kOffsetThreads / 32];
+// What the write kernel needs of a query, in shared memory.
+struct GatherInfo {
+  uint64_t capacity;
+  uint32_t *out_ids;
+  const uint32_t *bitmap;
+  const uint32_t *gcounts;
+  const unsigned long long *goff;
+  unsigned int *tiles_left;
+  unsigned long long *done_ns;
+  uint32_t ngroups, nrows;
+  int32_t nproj;
+  uint8_t proj_w[kMaxProj];
+  const uint8_t *proj_ptr[kMaxProj];
+  void *out_proj[kMaxProj];
+};
+
+__device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t *ent, uint32_t n, uint32_t row_ref,
+                                             unsigned long long pos_ref, int lane) {
+  const uint64_t cap = G.capacity;
+  for (uint32_t t0 = 0; t0 < n; t0 += 128) {
+    uint32_t row[4];
+    unsigned long long pos[4];
+    uint32_t ok = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t t = t0 + 32u * k + (uint32_t)lane;
+      row[k] = 0;
+      pos[k] = 0;
+      if (t < n) {
+        const uint32_t e = ent[t];
+        row[k] = row_ref + (e >> 16);
+        pos[k] = pos_ref + (e & 0xffffu);
+        if (pos[k] < cap) ok |= 1u << k;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if ((ok >> k) & 1u) G.out_ids[pos[k]] = row[k];
+    for (int c = 0; c < G.nproj; ++c) {
+      const int w = G.proj_w[c];
+      const uint8_t *src = G.proj_ptr[c];
+      void *dst = G.out_proj[c];
+      uint64_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((ok >> k) & 1u) v[k] = load_elem(src, row[k], w);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((ok >> k) & 1u) store_elem(dst, pos[k], v[k], w);
+    }
+  }
+}
+
+// One dense group, the whole warp: ids, then each projected column.
+__device__ __forceinline__ void dense_group(const GatherInfo &G, uint32_t g, uint32_t cnt, unsigned long long base,
+                                            unsigned long long *stg, int lane) {
+  const uint64_t cap = G.capacity;
+  const uint32_t word = __ldcg(&G.bitmap[(size_t)g * 8 + (lane >> 2)]);
+  const uint32_t bits8 = (word >> (8 * (lane & 3))) & 0xffu;
+  const uint32_t cl = __popc(bits8);
+  uint32_t incl = cl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t excl_l = incl - cl;
+  const uint32_t grow = g * kGroup;
+  {
+    uint32_t *sids = reinterpret_cast<uint32_t *>(stg);
+    uint32_t r = excl_l;
+    const uint32_t row_l = grow + 8u * (uint32_t)lane;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if ((bits8 >> k) & 1u) sids[r++] = row_l + (uint32_t)k;
+    __syncwarp();
+    for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
+      if (base + t < cap) G.out_ids[base + t] = sids[t];
+    __syncwarp();
+  }
+  for (int c = 0; c < G.nproj; ++c) {
+    const int w = G.proj_w[c];
+    const uint8_t *src = G.proj_ptr[c] + (size_t)grow * w;
+    void *dst = G.out_proj[c];
+    switch (w) {
+      case 1:
+        dense_column<uint8_t, 1>(src, static_cast<uint8_t *>(dst), reinterpret_cast<uint8_t *>(stg), bits8, excl_l,
+                                 cnt, base, cap, lane);
+        break;
+      case 2:
+        dense_column<uint16_t, 2>(src, static_cast<uint16_t *>(dst), reinterpret_cast<uint16_t *>(stg), bits8,
+                                  excl_l, cnt, base, cap, lane);
+        break;
+      case 4:
+        dense_column<uint32_t, 4>(src, static_cast<uint32_t *>(dst), reinterpret_cast<uint32_t *>(stg), bits8,
+                                  excl_l, cnt, base, cap, lane);
+        break;
+      default:
+        dense_column<unsigned long long, 8>(src, static_cast<unsigned long long *>(dst), stg, bits8, excl_l, cnt,
+                                            base, cap, lane);
+        break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_constant__ Launch L) {
+  __shared__ GatherInfo G;
+  __shared__ unsigned long long stage_buf[kWriteThreads / 32][kStageEntries / 2];
+  __shared__ uint32_t wsum[kWriteThreads / 32];
   __shared__ unsigned long long s_excl;
   __shared__ int s_q;
   const int lane = threadIdx.x & 31;
@@ -836,13 +959,33 @@ __global__ void __launch_bounds__(kOffsetThreads) offsets_kernel(const __grid_co
   if (threadIdx.x == 0) s_q = block_query(L, [](const Query *q) { return q->wunit_base; });
   __syncthreads();
   const Query *Q = query_ptr(L, s_q);
+  if (warp == 1) {
+    const int np = Q->nproj;
+    if (lane == 0) {
+      G.capacity = Q->capacity;
+      G.out_ids = Q->out_ids;
+      G.bitmap = Q->bitmap;
+      G.gcounts = Q->gcounts;
+      G.tiles_left = Q->tiles_left;
+      G.done_ns = Q->done_ns;
+      G.ngroups = Q->ngroups;
+      G.nrows = Q->nrows;
+      G.nproj = np;
+    }
+    if (lane < np) {
+      G.proj_w[lane] = Q->proj_w[lane];
+      G.proj_ptr[lane] = Q->proj_ptr[lane];
+      G.out_proj[lane] = Q->out_proj[lane];
+    }
+  }
   const uint32_t u = blockIdx.x - Q->wunit_base;
   const uint32_t urows = Q->unit_tiles * Q->tile_rows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
   const int ng = (int)((rows + kGroup - 1) / kGroup);
   const uint32_t g0 = urow0 / kGroup;
-  const uint32_t c = (int)threadIdx.x < ng ? Q->gcounts[g0 + threadIdx.x] : 0u;
+  const bool valid = (int)threadIdx.x < ng;
+  const uint32_t c = valid ? Q->gcounts[g0 + threadIdx.x] : 0u;
   uint32_t inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -894,219 +1037,62 @@ __global__ void __launch_bounds__(kOffsetThreads) offsets_kernel(const __grid_co
   __syncthreads();
   uint32_t wbase = 0;
   for (int i = 0; i < warp; ++i) wbase += wsum[i];
-  if ((int)threadIdx.x < ng) Q->goff[g0 + threadIdx.x] = s_excl + wbase + inc - c;
-}
-
-// Copies staged sparse entries (row within the warp's groups << 16 | output
-// slot relative to the warp's first group) to the outputs: 4 entries per
-// lane, each column's loads issued before its stores.
-__device__ __forceinline__ void flush_sparse(const struct GatherInfo &G, const uint32_t *ent, uint32_t n,
-                                             uint32_t row_ref, unsigned long long pos_ref, int lane);
-
-// What the gather kernel needs of a query, in shared memory.
-struct GatherInfo {
-  uint64_t capacity;
-  uint32_t *out_ids;
-  const uint32_t *bitmap;
-  const uint32_t *gcounts;
-  const unsigned long long *goff;
-  unsigned int *tiles_left;
-  unsigned long long *done_ns;
-  uint32_t ngroups, nrows, gblock_base;
-  int32_t nproj;
-  uint8_t proj_w[kMaxProj];
-  const uint8_t *proj_ptr[kMaxProj];
-  void *out_proj[kMaxProj];
-};
-
-__device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t *ent, uint32_t n, uint32_t row_ref,
-                                             unsigned long long pos_ref, int lane) {
-  const uint64_t cap = G.capacity;
-  for (uint32_t t0 = 0; t0 < n; t0 += 128) {
-    uint32_t row[4];
-    unsigned long long pos[4];
-    uint32_t ok = 0;
+  const uint32_t wtot = wsum[warp];
+  if (wtot != 0) {
+    const uint64_t cap = G.capacity;
+    const unsigned long long pos_ref = s_excl + wbase;      // first slot of the warp's groups
+    const unsigned long long base_l = pos_ref + inc - c;    // first slot of this lane's group
+    const uint32_t grp_l = g0 + threadIdx.x;
+    const uint32_t grow_l = grp_l * kGroup;
+    const bool dense_l = valid && c >= kDenseMin && grow_l + kGroup <= G.nrows;
+    unsigned long long *stg = stage_buf[warp];
+    for (uint32_t dm = __ballot_sync(FULL, dense_l); dm; dm &= dm - 1) {
+      const int j = __ffs(dm) - 1;
+      const unsigned long long base = __shfl_sync(FULL, base_l, j);
+      if (base < cap) dense_group(G, __shfl_sync(FULL, grp_l, j), __shfl_sync(FULL, c, j), base, stg, lane);
+    }
+    // the other groups: lane = group, entries staged in slot order
+    const uint32_t sc = dense_l ? 0u : c;
+    uint32_t sx = sc;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t t = t0 + 32u * k + (uint32_t)lane;
-      row[k] = 0;
-      pos[k] = 0;
-      if (t < n) {
-        const uint32_t e = ent[t];
-        row[k] = row_ref + (e >> 16);
-        pos[k] = pos_ref + (e & 0xffffu);
-        if (pos[k] < cap) ok |= 1u << k;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, sx, o);
+      if (lane >= o) sx += y;
+    }
+    const uint32_t stot = __shfl_sync(FULL, sx, 31);
+    sx -= sc;
+    if (stot != 0) {
+      uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
+      if (sc != 0) {
+        const uint4 *bw = reinterpret_cast<const uint4 *>(G.bitmap + (size_t)grp_l * 8);
+        wlo = __ldcg(bw);
+        whi = __ldcg(bw + 1);
       }
-    }
+      const uint32_t words[8] = {wlo.x, wlo.y, wlo.z, wlo.w, whi.x, whi.y, whi.z, whi.w};
+      const uint32_t row_ref = (g0 + 32u * (uint32_t)warp) * kGroup;
+      const uint32_t rrel = grow_l - row_ref;
+      const uint32_t srel = (uint32_t)(base_l - pos_ref);
+      uint32_t *ent = reinterpret_cast<uint32_t *>(stg);
+      for (uint32_t win = 0; win < stot; win += kStageEntries) {
+        const uint32_t wend = win + kStageEntries;
+        if (sc != 0 && sx < wend && sx + sc > win) {
+          // the group's first sc set bits are its rows (in the table's last
+          // group, words past the last row were never written: never read past sc)
+          const uint32_t eend = min(wend, sx + sc);
+          uint32_t e = sx;  // staged index of this lane's next entry
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if ((ok >> k) & 1u) G.out_ids[pos[k]] = row[k];
-    for (int c = 0; c < G.nproj; ++c) {
-      const int w = G.proj_w[c];
-      const uint8_t *src = G.proj_ptr[c];
-      void *dst = G.out_proj[c];
-      uint64_t v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if ((ok >> k) & 1u) v[k] = load_elem(src, row[k], w);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if ((ok >> k) & 1u) store_elem(dst, pos[k], v[k], w);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kGatherThreads) gather_kernel(const __grid_constant__ Launch L) {
-  __shared__ GatherInfo G;
-  __shared__ unsigned long long stage_buf[kGatherThreads / 32][kGroup];  // per-warp staging (dense groups)
-  __shared__ int s_q;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_q = block_query(L, [](const Query *q) { return q->gblock_base; });
-  __syncthreads();
-  if (warp == 0) {
-    const Query *Q = query_ptr(L, s_q);
-    const int np = Q->nproj;
-    if (lane == 0) {
-      G.capacity = Q->capacity;
-      G.out_ids = Q->out_ids;
-      G.bitmap = Q->bitmap;
-      G.gcounts = Q->gcounts;
-      G.goff = Q->goff;
-      G.tiles_left = Q->tiles_left;
-      G.done_ns = Q->done_ns;
-      G.ngroups = Q->ngroups;
-      G.nrows = Q->nrows;
-      G.gblock_base = Q->gblock_base;
-      G.nproj = np;
-    }
-    if (lane < np) {
-      G.proj_w[lane] = Q->proj_w[lane];
-      G.proj_ptr[lane] = Q->proj_ptr[lane];
-      G.out_proj[lane] = Q->out_proj[lane];
-    }
-  }
-  __syncthreads();
-  const uint64_t cap = G.capacity;
-  const int np = G.nproj;
-  const uint32_t wg0 = (blockIdx.x - G.gblock_base) * kGatherGroups + (uint32_t)warp * kGatherGroupsPerWarp;
-  // this warp's 8 groups: counts and offsets (lanes 0..7), bitmap words (lane 8i+p: group i, word p)
-  const uint32_t gl = wg0 + (uint32_t)(lane & 7);
-  uint32_t cnt_l = 0;
-  unsigned long long off_l = 0;
-  if (lane < 8 && gl < G.ngroups) {
-    cnt_l = G.gcounts[gl];
-    off_l = G.goff[gl];
-  }
-  const uint32_t ga = wg0 + (uint32_t)(lane >> 3), gb = ga + 4;
-  const uint32_t wa = ga < G.ngroups ? __ldcg(&G.bitmap[(size_t)ga * 8 + (lane & 7)]) : 0u;
-  const uint32_t wb = gb < G.ngroups ? __ldcg(&G.bitmap[(size_t)gb * 8 + (lane & 7)]) : 0u;
-  // sparse entries staged in the warp's buffer, relative to the warp's first group
-  const uint32_t row_ref = wg0 * kGroup;
-  const unsigned long long pos_ref = __shfl_sync(FULL, off_l, 0);
-  uint32_t *ent = reinterpret_cast<uint32_t *>(stage_buf[warp]);
-  uint32_t nent = 0;
-  for (int i = 0; i < kGatherGroupsPerWarp; ++i) {
-    const uint32_t g = wg0 + (uint32_t)i;
-    if (g >= G.ngroups) break;
-    const uint32_t cnt = __shfl_sync(FULL, cnt_l, i);
-    if (cnt == 0) continue;
-    const unsigned long long base = __shfl_sync(FULL, off_l, i);
-    if (base >= cap) continue;
-    uint32_t bal[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) bal[p] = __shfl_sync(FULL, i < 4 ? wa : wb, 8 * (i & 3) + p);
-    const uint32_t grow = g * kGroup;  // table row of the group's first row
-    if (cnt > 96 && grow + kGroup <= G.nrows) {
-      if (nent) {  // the staging buffer is needed: write the staged sparse entries first
-        __syncwarp();
-        flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
-        __syncwarp();
-        nent = 0;
-      }
-      const uint32_t wsel = lane >> 2;
-      const uint32_t word = wsel == 0 ? bal[0] : wsel == 1 ? bal[1] : wsel == 2 ? bal[2] : wsel == 3 ? bal[3]
-                          : wsel == 4 ? bal[4] : wsel == 5 ? bal[5] : wsel == 6 ? bal[6] : bal[7];
-      const uint32_t bits8 = (word >> (8 * (lane & 3))) & 0xffu;
-      const uint32_t cl = __popc(bits8);
-      uint32_t incl = cl;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t excl_l = incl - cl;
-      {
-        uint32_t *sids = reinterpret_cast<uint32_t *>(stage_buf[warp]);
-        uint32_t r = excl_l;
-        const uint32_t row_l = grow + 8u * (uint32_t)lane;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if ((bits8 >> k) & 1u) sids[r++] = row_l + (uint32_t)k;
-        __syncwarp();
-        for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
-          if (base + t < cap) G.out_ids[base + t] = sids[t];
-        __syncwarp();
-      }
-      for (int c = 0; c < np; ++c) {
-        const int w = G.proj_w[c];
-        const uint8_t *src = G.proj_ptr[c] + (size_t)grow * w;
-        void *dst = G.out_proj[c];
-        switch (w) {
-          case 1:
-            dense_column<uint8_t, 1>(src, static_cast<uint8_t *>(dst), reinterpret_cast<uint8_t *>(stage_buf[warp]),
-                                     bits8, excl_l, cnt, base, cap, lane);
-            break;
-          case 2:
-            dense_column<uint16_t, 2>(src, static_cast<uint16_t *>(dst),
-                                      reinterpret_cast<uint16_t *>(stage_buf[warp]), bits8, excl_l, cnt, base, cap,
-                                      lane);
-            break;
-          case 4:
-            dense_column<uint32_t, 4>(src, static_cast<uint32_t *>(dst),
-                                      reinterpret_cast<uint32_t *>(stage_buf[warp]), bits8, excl_l, cnt, base, cap,
-                                      lane);
-            break;
-          default:
-            dense_column<unsigned long long, 8>(src, static_cast<unsigned long long *>(dst), stage_buf[warp], bits8,
-                                                excl_l, cnt, base, cap, lane);
-            break;
-        }
-      }
-      continue;
-    }
-    // the group's j-th qualifying row: entry nent + j of the staging buffer
-    if (nent + cnt > 256) {
-      __syncwarp();
-      flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
-      __syncwarp();
-      nent = 0;
-    }
-    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
-      const uint32_t j = j0 + (uint32_t)lane;
-      if (j < cnt) {
-        uint32_t cum = 0, sel = 0, r = 0, pp = 0;
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const uint32_t cc = __popc(bal[p]);
-          if (j >= cum && j < cum + cc) {
-            sel = bal[p];
-            r = j - cum;
-            pp = (uint32_t)p;
+          for (int p = 0; p < 8; ++p) {
+            for (uint32_t x = words[p]; x != 0 && e < eend; x &= x - 1, ++e)
+              if (e >= win) ent[e - win] = ((rrel + 32u * p + (uint32_t)(__ffs(x) - 1)) << 16) | (srel + e - sx);
           }
-          cum += cc;
         }
-        const uint32_t row = grow + 32u * pp + nth_set_bit(sel, r);
-        ent[nent + j] = ((row - row_ref) << 16) | (uint32_t)(base - pos_ref + j);
+        __syncwarp();
+        flush_sparse(G, ent, min(stot - win, kStageEntries), row_ref, pos_ref, lane);
+        __syncwarp();
       }
     }
-    nent += cnt;
   }
-  if (nent) {
-    __syncwarp();
-    flush_sparse(G, ent, nent, row_ref, pos_ref, lane);
-  }
-  // per-query completion time: the query's last gather block
+  // per-query completion time: the query's last write block
   if (G.done_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1241,27 +1227,22 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
   return ESC_OK;
 }
 
-// Second pass of compaction: group offsets (one block per unit), then the
-// gather (one block per 64 groups).
-esc_status launch_write(const Launch &L, uint32_t unit_blocks, uint32_t gather_blocks, cudaStream_t st) {
+// Second pass of compaction: the write kernel, one block per work unit.
+esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) {
   if (unit_blocks == 0) return ESC_OK;
-  offsets_kernel<<<unit_blocks, kOffsetThreads, 0, st>>>(L);
-  ESC_CK(cudaGetLastError());
-  gather_kernel<<<gather_blocks, kGatherThreads, 0, st>>>(L);
+  write_kernel<<<unit_blocks, kWriteThreads, 0, st>>>(L);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
 
-uint32_t gather_blocks_for(const Query &q) { return (q.ngroups + kGatherGroups - 1) / kGatherGroups; }
-
 // Compaction scratch of one query: unit totals and look-back words (both
-// zeroed before the scan), then the selection bitmap and group counts (fully
-// written by the scan before the write kernel reads them).
+// zeroed before the scan), then the selection bitmap and group counts (the
+// scan writes every group count, and the bitmap words of every group with a
+// qualifying row, before the write kernel reads them).
 size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
 size_t select_other_bytes(const Query &q) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
-  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255) +
-         ((groups * 8 + 255) & ~(size_t)255);
+  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255);
 }
 void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   q.unit_total = reinterpret_cast<unsigned long long *>(zeroed);
@@ -1269,8 +1250,6 @@ void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
   q.bitmap = reinterpret_cast<uint32_t *>(other);
   q.gcounts = reinterpret_cast<uint32_t *>(other + ((groups * 32 + 255) & ~(size_t)255));
-  q.goff = reinterpret_cast<unsigned long long *>(other + ((groups * 32 + 255) & ~(size_t)255) +
-                                                  ((groups * 4 + 255) & ~(size_t)255));
 }
 
 // Validates a (table, pred, rows) call and fills the per-call query.
@@ -1341,7 +1320,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.q0.count = dev_count ? dev_count : &sc->count;
   if (mode == MODE_SELECT) select_bind(L.q0, base + head, base + head + zeroed);
   s = launch_scan(L, st);
-  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, gather_blocks_for(L.q0), st);
+  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
     return s;
@@ -1423,7 +1402,6 @@ struct esc_batch {
   int device = 0;
   uint32_t total_units = 0;
   uint32_t write_blocks = 0;
-  uint32_t gather_blocks = 0;
   void *dev_mem = nullptr;          // queries + scratch, owned
   Query *queries = nullptr;         // device
   uint8_t *scratch = nullptr;       // device: hdr, counts, done, countdowns, unit words
@@ -1459,7 +1437,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
-  uint64_t units = 0, wunits = 0, gblocks = 0, zeroed = 0, other = 0;
+  uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
@@ -1468,11 +1446,9 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       return s;
     qs[i].unit_base = (uint32_t)units;
     qs[i].wunit_base = (uint32_t)wunits;
-    qs[i].gblock_base = (uint32_t)gblocks;
     units += qs[i].nunits;
     if (compact) {
       wunits += qs[i].nunits;
-      gblocks += gather_blocks_for(qs[i]);
       zeroed += select_zeroed_bytes(qs[i]);
       other += select_other_bytes(qs[i]);
     }
@@ -1484,7 +1460,6 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   cudaGetDevice(&b->device);
   b->total_units = (uint32_t)units;
   b->write_blocks = (uint32_t)wunits;
-  b->gather_blocks = (uint32_t)gblocks;
   // device memory: queries | zeroed every run: header, counts, done times,
   // countdowns, unit totals + look-back words | countdown initial values |
   // selection bitmaps + group counts
@@ -1517,7 +1492,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
-      init[i] = gather_blocks_for(qs[i]);            // counted down by the gather kernel
+      init[i] = qs[i].nunits;                         // counted down by the write kernel
     } else {
       init[i] = qs[i].ntiles * (unsigned)kConsumers;  // counted down by the scan kernel
     }
@@ -1551,7 +1526,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
     ls = launch_scan(L, cs);
-    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, b->gather_blocks, cs);
+    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
   if (e == cudaSuccess && ls == ESC_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -1620,7 +1595,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   if (n < 1 || !tables || !preds || !dev_counts)
     return fail(ESC_EINVAL, "esc_selectivity_batch_async: need n >= 1 tables, predicates and dev_counts");
   std::vector<Query> qs((size_t)n);
-  uint64_t units = 0, wunits = 0, gblocks = 0, zeroed = 0, other = 0;
+  uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
   esc_status s;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
@@ -1630,11 +1605,9 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       return s;
     qs[i].unit_base = (uint32_t)units;
     qs[i].wunit_base = (uint32_t)wunits;
-    qs[i].gblock_base = (uint32_t)gblocks;
     units += qs[i].nunits;
     if (compact) {
       wunits += qs[i].nunits;
-      gblocks += gather_blocks_for(qs[i]);
       zeroed += select_zeroed_bytes(qs[i]);
       other += select_other_bytes(qs[i]);
     }
@@ -1664,7 +1637,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
-      init[i] = gather_blocks_for(qs[i]);
+      init[i] = qs[i].nunits;
     } else {
       init[i] = qs[i].ntiles * (unsigned)kConsumers;
     }
@@ -1684,7 +1657,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   L.total_units = (uint32_t)units;
   L.hdr = reinterpret_cast<ScratchHdr *>(z);
   s = launch_scan(L, st);
-  if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, (uint32_t)gblocks, st);
+  if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, st);
   if (s == ESC_OK) {
     e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && dev_done_ns)
@@ -1830,9 +1803,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
     scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
-      offsets_kernel<<<q.nunits, kOffsetThreads, 0, st>>>(L);
-      ESC_CK(cudaGetLastError());
-      gather_kernel<<<(q.ngroups + kGatherGroups - 1) / kGatherGroups, kGatherThreads, 0, st>>>(L);
+      write_kernel<<<q.nunits, kWriteThreads, 0, st>>>(L);
       ESC_CK(cudaGetLastError());
     }
   }
