@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
 //     and never waits.
 //  2. Each group's first slot: a block-wide exclusive scan of the group
 //     counts of the unit.
-//  3. Warp w writes groups 32w .. 32w+31 of the unit.  A dense group (at least
+//  3. The unit's groups are split evenly over the warps (at most 32 each).  A dense group (at least
 //     kDenseMin qualifying rows, all 256 rows inside the table) takes the
 //     whole warp: 16-byte vector loads of the projected columns (lane l: rows
 //     8l .. 8l+7), staged in shared memory at their output slots, stored with
@@ -762,8 +762,25 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
 //     copies the staged entries, 4 per lane, loads before stores.
 
 constexpr int kWriteThreads = 256;
-constexpr uint32_t kDenseMin = 97;
-constexpr uint32_t kStageEntries = 512;  // sparse entries staged per warp (2 KB)
+constexpr int kWriteWarps = kWriteThreads / 32;
+constexpr uint32_t kDenseMin = 97;       // qualifying rows of a group for the dense path
+constexpr uint32_t kRawBytes = 2048;     // per warp: a dense group's projected values (<= 8 B per row at once)
+constexpr uint32_t kStageEntries = kRawBytes / 4;  // sparse entries staged per warp (same buffer)
+
+// Shared memory of one warp of the write kernel.
+struct WriteWarpSmem {
+  uint32_t words[32][8];                 // bitmap words of the warp's groups
+  uint32_t sids[kGroup];                 // dense group: row (within the group) of each output slot
+  __align__(16) uint8_t raw[kRawBytes];  // dense group: projected columns in row order; else sparse entries
+};
+constexpr size_t kWriteSmem = sizeof(WriteWarpSmem) * kWriteWarps;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 __device__ __forceinline__ uint64_t load_elem(const uint8_t *base, uint32_t row, int w) {
   switch (w) {
@@ -781,54 +798,6 @@ __device__ __forceinline__ void store_elem(void *base, unsigned long long pos, u
     case 4: static_cast<uint32_t *>(base)[pos] = (uint32_t)v; break;
     default: static_cast<unsigned long long *>(base)[pos] = v; break;
   }
-}
-
-template <int W>
-__device__ __forceinline__ void load8_row_major(const uint8_t *p, uint64_t (&v)[8]) {
-  if (W == 1) {
-    const uint2 x = *reinterpret_cast<const uint2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      v[k] = (x.x >> (8 * k)) & 0xffu;
-      v[k + 4] = (x.y >> (8 * k)) & 0xffu;
-    }
-  } else if (W == 2) {
-    const uint4 x = *reinterpret_cast<const uint4 *>(p);
-    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      v[2 * k] = w[k] & 0xffffu;
-      v[2 * k + 1] = w[k] >> 16;
-    }
-  } else if (W == 4) {
-    const uint4 a = reinterpret_cast<const uint4 *>(p)[0];
-    const uint4 b = reinterpret_cast<const uint4 *>(p)[1];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  } else {
-    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const ulonglong2 x = q[k];
-      v[2 * k] = x.x;
-      v[2 * k + 1] = x.y;
-    }
-  }
-}
-
-template <typename T, int W>
-__device__ __forceinline__ void dense_column(const uint8_t *src_rows, T *dst, T *stg, uint32_t bits8, uint32_t excl_l,
-                                             uint32_t cnt, unsigned long long base, uint64_t cap, int lane) {
-  uint64_t v[8];
-  load8_row_major<W>(src_rows + (size_t)lane * 8 * W, v);
-  uint32_t r = excl_l;
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if ((bits8 >> k) & 1u) stg[r++] = (T)v[k];
-  __syncwarp();
-  for (uint32_t i = (uint32_t)lane; i < cnt; i += 32)
-    if (base + i < cap) dst[base + i] = stg[i];
-  __syncwarp();
 }
 
 // Finds the query a block belongs to: the last one whose first block (the
@@ -859,6 +828,9 @@ struct GatherInfo {
   void *out_proj[kMaxProj];
 };
 
+// Copies staged sparse entries (row within the warp's groups << 16 | output
+// slot relative to the warp's first group) to the outputs: 4 entries per
+// lane, each column's loads issued before its stores.
 __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t *ent, uint32_t n, uint32_t row_ref,
                                              unsigned long long pos_ref, int lane) {
   const uint64_t cap = G.capacity;
@@ -896,12 +868,14 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
   }
 }
 
-// One dense group, the whole warp: ids, then each projected column.
-__device__ __forceinline__ void dense_group(const GatherInfo &G, uint32_t g, uint32_t cnt, unsigned long long base,
-                                            unsigned long long *stg, int lane) {
+// One dense group, the whole warp.  The projected columns of all 256 rows
+// arrive together (16-byte asynchronous copies, at most kRawBytes at a
+// time; a column wider than that is read in place); each output slot then
+// takes its row's value from shared memory, so that the stores coalesce.
+__device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &W, int j, uint32_t g, uint32_t cnt,
+                                            unsigned long long base, int lane) {
   const uint64_t cap = G.capacity;
-  const uint32_t word = __ldcg(&G.bitmap[(size_t)g * 8 + (lane >> 2)]);
-  const uint32_t bits8 = (word >> (8 * (lane & 3))) & 0xffu;
+  const uint32_t bits8 = (W.words[j][lane >> 2] >> (8 * (lane & 3))) & 0xffu;
   const uint32_t cl = __popc(bits8);
   uint32_t incl = cl;
 #pragma unroll
@@ -909,53 +883,58 @@ __device__ __forceinline__ void dense_group(const GatherInfo &G, uint32_t g, uin
     const uint32_t y = __shfl_up_sync(FULL, incl, o);
     if (lane >= o) incl += y;
   }
-  const uint32_t excl_l = incl - cl;
-  const uint32_t grow = g * kGroup;
-  {
-    uint32_t *sids = reinterpret_cast<uint32_t *>(stg);
-    uint32_t r = excl_l;
-    const uint32_t row_l = grow + 8u * (uint32_t)lane;
+  uint32_t r = incl - cl;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if ((bits8 >> k) & 1u) sids[r++] = row_l + (uint32_t)k;
-    __syncwarp();
-    for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
-      if (base + t < cap) G.out_ids[base + t] = sids[t];
-    __syncwarp();
-  }
-  for (int c = 0; c < G.nproj; ++c) {
-    const int w = G.proj_w[c];
-    const uint8_t *src = G.proj_ptr[c] + (size_t)grow * w;
-    void *dst = G.out_proj[c];
-    switch (w) {
-      case 1:
-        dense_column<uint8_t, 1>(src, static_cast<uint8_t *>(dst), reinterpret_cast<uint8_t *>(stg), bits8, excl_l,
-                                 cnt, base, cap, lane);
-        break;
-      case 2:
-        dense_column<uint16_t, 2>(src, static_cast<uint16_t *>(dst), reinterpret_cast<uint16_t *>(stg), bits8,
-                                  excl_l, cnt, base, cap, lane);
-        break;
-      case 4:
-        dense_column<uint32_t, 4>(src, static_cast<uint32_t *>(dst), reinterpret_cast<uint32_t *>(stg), bits8,
-                                  excl_l, cnt, base, cap, lane);
-        break;
-      default:
-        dense_column<unsigned long long, 8>(src, static_cast<unsigned long long *>(dst), stg, bits8, excl_l, cnt,
-                                            base, cap, lane);
-        break;
+  for (int k = 0; k < 8; ++k)
+    if ((bits8 >> k) & 1u) W.sids[r++] = 8u * (uint32_t)lane + (uint32_t)k;
+  const uint32_t grow = g * kGroup;
+  const int np = G.nproj;
+  int c0 = 0;
+  do {
+    // columns c0 .. c1-1 share the buffer (a single column always goes, in place if too wide)
+    int c1 = c0;
+    uint32_t off = 0;
+    while (c1 < np && (c1 == c0 || off + kGroup * G.proj_w[c1] <= kRawBytes)) off += kGroup * G.proj_w[c1++];
+    const bool staged = off <= kRawBytes;
+    if (staged) {
+      off = 0;
+      for (int c = c0; c < c1; ++c) {
+        const uint32_t bytes = kGroup * G.proj_w[c];
+        const uint8_t *src = G.proj_ptr[c] + (size_t)grow * G.proj_w[c];
+        for (uint32_t x = 16u * (uint32_t)lane; x < bytes; x += 512u) cp_async16(W.raw + off + x, src + x);
+        off += bytes;
+      }
     }
-  }
+    if (c0 == 0) {
+      __syncwarp();
+      for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
+        if (base + t < cap) G.out_ids[base + t] = grow + W.sids[t];
+    }
+    if (staged) cp_async_wait_all();
+    __syncwarp();
+    off = 0;
+    for (int c = c0; c < c1; ++c) {
+      const int w = G.proj_w[c];
+      void *dst = G.out_proj[c];
+      const uint8_t *col = staged ? W.raw + off : G.proj_ptr[c] + (size_t)grow * w;
+      for (uint32_t t = (uint32_t)lane; t < cnt; t += 32)
+        if (base + t < cap) store_elem(dst, base + t, load_elem(col, W.sids[t], w), w);
+      off += kGroup * w;
+    }
+    __syncwarp();
+    c0 = c1;
+  } while (c0 < np);
 }
 
-__global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_constant__ Launch L) {
+  extern __shared__ __align__(16) uint8_t wsmem[];
   __shared__ GatherInfo G;
-  __shared__ unsigned long long stage_buf[kWriteThreads / 32][kStageEntries / 2];
-  __shared__ uint32_t wsum[kWriteThreads / 32];
+  __shared__ uint32_t wsum[kWriteWarps];
   __shared__ unsigned long long s_excl;
   __shared__ int s_q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  WriteWarpSmem &W = reinterpret_cast<WriteWarpSmem *>(wsmem)[warp];
   if (threadIdx.x == 0) s_q = block_query(L, [](const Query *q) { return q->wunit_base; });
   __syncthreads();
   const Query *Q = query_ptr(L, s_q);
@@ -984,8 +963,21 @@ __global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_const
   const uint32_t rows = min(urows, Q->nrows - urow0);
   const int ng = (int)((rows + kGroup - 1) / kGroup);
   const uint32_t g0 = urow0 / kGroup;
-  const bool valid = (int)threadIdx.x < ng;
-  const uint32_t c = valid ? Q->gcounts[g0 + threadIdx.x] : 0u;
+  // warp w: groups w*gpw .. w*gpw+gpw-1 of the unit, lane = group
+  const int gpw = (ng + kWriteWarps - 1) / kWriteWarps;
+  const int gi = warp * gpw + lane;
+  const bool valid = lane < gpw && gi < ng;
+  const uint32_t grp_l = g0 + (uint32_t)gi;
+  // the group's count and bitmap words in one round trip (the scan wrote the
+  // words of every group with a qualifying row; the others are never used)
+  uint32_t c = 0;
+  uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
+  if (valid) {
+    const uint4 *bw = reinterpret_cast<const uint4 *>(Q->bitmap + (size_t)grp_l * 8);
+    c = Q->gcounts[grp_l];
+    wlo = __ldcg(bw);
+    whi = __ldcg(bw + 1);
+  }
   uint32_t inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1037,19 +1029,21 @@ __global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_const
   __syncthreads();
   uint32_t wbase = 0;
   for (int i = 0; i < warp; ++i) wbase += wsum[i];
-  const uint32_t wtot = wsum[warp];
-  if (wtot != 0) {
-    const uint64_t cap = G.capacity;
+  if (wsum[warp] != 0) {
     const unsigned long long pos_ref = s_excl + wbase;      // first slot of the warp's groups
     const unsigned long long base_l = pos_ref + inc - c;    // first slot of this lane's group
-    const uint32_t grp_l = g0 + threadIdx.x;
     const uint32_t grow_l = grp_l * kGroup;
     const bool dense_l = valid && c >= kDenseMin && grow_l + kGroup <= G.nrows;
-    unsigned long long *stg = stage_buf[warp];
-    for (uint32_t dm = __ballot_sync(FULL, dense_l); dm; dm &= dm - 1) {
+    const uint32_t dm0 = __ballot_sync(FULL, dense_l);
+    if (dm0) {
+      *reinterpret_cast<uint4 *>(&W.words[lane][0]) = wlo;
+      *reinterpret_cast<uint4 *>(&W.words[lane][4]) = whi;
+      __syncwarp();
+    }
+    for (uint32_t dm = dm0; dm; dm &= dm - 1) {
       const int j = __ffs(dm) - 1;
       const unsigned long long base = __shfl_sync(FULL, base_l, j);
-      if (base < cap) dense_group(G, __shfl_sync(FULL, grp_l, j), __shfl_sync(FULL, c, j), base, stg, lane);
+      if (base < G.capacity) dense_group(G, W, j, __shfl_sync(FULL, grp_l, j), __shfl_sync(FULL, c, j), base, lane);
     }
     // the other groups: lane = group, entries staged in slot order
     const uint32_t sc = dense_l ? 0u : c;
@@ -1062,27 +1056,21 @@ __global__ void __launch_bounds__(kWriteThreads) write_kernel(const __grid_const
     const uint32_t stot = __shfl_sync(FULL, sx, 31);
     sx -= sc;
     if (stot != 0) {
-      uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
-      if (sc != 0) {
-        const uint4 *bw = reinterpret_cast<const uint4 *>(G.bitmap + (size_t)grp_l * 8);
-        wlo = __ldcg(bw);
-        whi = __ldcg(bw + 1);
-      }
-      const uint32_t words[8] = {wlo.x, wlo.y, wlo.z, wlo.w, whi.x, whi.y, whi.z, whi.w};
-      const uint32_t row_ref = (g0 + 32u * (uint32_t)warp) * kGroup;
+      const uint32_t row_ref = (g0 + (uint32_t)(warp * gpw)) * kGroup;
       const uint32_t rrel = grow_l - row_ref;
       const uint32_t srel = (uint32_t)(base_l - pos_ref);
-      uint32_t *ent = reinterpret_cast<uint32_t *>(stg);
+      uint32_t *ent = reinterpret_cast<uint32_t *>(W.raw);
       for (uint32_t win = 0; win < stot; win += kStageEntries) {
         const uint32_t wend = win + kStageEntries;
         if (sc != 0 && sx < wend && sx + sc > win) {
-          // the group's first sc set bits are its rows (in the table's last
-          // group, words past the last row were never written: never read past sc)
+          // the group's first sc set bits are its rows: never read past sc
           const uint32_t eend = min(wend, sx + sc);
           uint32_t e = sx;  // staged index of this lane's next entry
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
-            for (uint32_t x = words[p]; x != 0 && e < eend; x &= x - 1, ++e)
+            const uint4 &h = p < 4 ? wlo : whi;
+            const uint32_t wp = (p & 3) == 0 ? h.x : (p & 3) == 1 ? h.y : (p & 3) == 2 ? h.z : h.w;
+            for (uint32_t x = wp; x != 0 && e < eend; x &= x - 1, ++e)
               if (e >= win) ent[e - win] = ((rrel + 32u * p + (uint32_t)(__ffs(x) - 1)) << 16) | (srel + e - sx);
           }
         }
@@ -1148,6 +1136,7 @@ esc_status device_state(DeviceState **out) {
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
     ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
     cudaMemPoolProps props;
@@ -1230,7 +1219,7 @@ esc_status launch_scan(const Launch &L, cudaStream_t st) {
 // Second pass of compaction: the write kernel, one block per work unit.
 esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) {
   if (unit_blocks == 0) return ESC_OK;
-  write_kernel<<<unit_blocks, kWriteThreads, 0, st>>>(L);
+  write_kernel<<<unit_blocks, kWriteThreads, kWriteSmem, st>>>(L);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
@@ -1739,6 +1728,7 @@ esc_status noalloc_device(NoAllocDevice **out) {
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
     ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
     void *p = nullptr;
@@ -1803,7 +1793,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
     scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
-      write_kernel<<<q.nunits, kWriteThreads, 0, st>>>(L);
+      write_kernel<<<q.nunits, kWriteThreads, kWriteSmem, st>>>(L);
       ESC_CK(cudaGetLastError());
     }
   }
