@@ -172,8 +172,8 @@ esc_status esc_selectivity_async(const esc_table *table, const esc_pred *pred,
  * cudaMalloc, cudaFree or other allocating routine: its scratch is a 12 MiB
  * array built into the library, reserved on every device that loads the
  * library until the process exits.  Counting alone fits any table; with
- * `rows` (materialisation) the table may have up to about 85 million rows
- * (the scratch needs about nrows/7 bytes); larger tables give ESC_EINVAL.
+ * `rows` (materialisation) the table may have up to about 95 million rows
+ * (the scratch needs about nrows/8 bytes); larger tables give ESC_EINVAL.
  * The first call on a device looks up the array's device address (no
  * allocation); make that first call before any stream capture.  Every call
  * shares the one array: calls whose GPU work overlaps (different streams,

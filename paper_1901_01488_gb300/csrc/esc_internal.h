@@ -65,9 +65,8 @@ struct Instr {
 static_assert(sizeof(Instr) == 32, "Instr layout");
 
 // MODE_COUNT: exact count.  MODE_BITMAP: count + caller's dense-key bitmap.
-// MODE_SELECT: first pass of ordered compaction: count + selection bitmap,
-// per-group counts and per-unit totals in scratch; the write kernel then
-// materialises the rows.
+// MODE_SELECT: first pass of ordered compaction: count + selection bitmap and
+// per-unit totals in scratch; the write kernel then materialises the rows.
 enum Mode : int32_t { MODE_COUNT = 0, MODE_SELECT = 1, MODE_BITMAP = 2 };
 
 // One sub-query as the scan kernel sees it.  Built on the host per call (or
@@ -99,7 +98,7 @@ struct Query {
   uint32_t *bitmap;               // MODE_BITMAP: caller's bitmap; MODE_SELECT: selection bitmap scratch
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
-  uint32_t *gcounts;              // MODE_SELECT: qualifying rows per 256-row group (scratch)
+  void *pad3;
   void *pad2;
   unsigned long long *unit_total; // MODE_SELECT: qualifying rows per unit (zeroed)
   unsigned long long *unit_status;// write kernel's decoupled look-back words, one per unit (zeroed)

@@ -83,6 +83,16 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Shared -> global bulk copy (async proxy), tracked by bulk groups.
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -512,6 +522,12 @@ __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned l
   }
 }
 
+// Compaction results of one tile (the selection bitmap, 32 B per group),
+// staged in shared memory and written with one bulk copy by the tile's last
+// consumer.
+constexpr size_t kResGroups = kMaxTileRows / kGroup;
+constexpr size_t kResBytes = kResGroups * 32;
+
 // Shared-memory layout of the scan kernel (offsets in bytes).
 struct SmemLayout {
   static constexpr size_t stages = 0;
@@ -520,7 +536,9 @@ struct SmemLayout {
   static constexpr size_t meta = bars + 2 * kStages * 8;
   static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);      // [S] int32
   static constexpr size_t take = slotq + kStages * 4;                       // [S] u32 pair claims
-  static constexpr size_t total = take + kStages * 4;
+  static constexpr size_t resdone = take + kStages * 4;                     // [S] u32 warps done (compaction)
+  static constexpr size_t res = (resdone + kStages * 4 + 127) & ~(size_t)127;  // [S] compaction results
+  static constexpr size_t total = res + kStages * kResBytes;
 };
 
 // ------------------------------------------------------------------ the scan kernel
@@ -535,6 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SmemLayout::meta);
   int32_t *slotq = reinterpret_cast<int32_t *>(smem + SmemLayout::slotq);
   uint32_t *take = reinterpret_cast<uint32_t *>(smem + SmemLayout::take);
+  uint32_t *resdone = reinterpret_cast<uint32_t *>(smem + SmemLayout::resdone);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -545,6 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], kConsumers);
       slotq[s] = -1;
+      resdone[s] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -556,11 +576,19 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
     uint32_t phase = 0;
     int qc = 0;  // cursor over queries: tickets of one CTA only increase
     bool done = false;
+    // The next unit's ticket and the abort flag are fetched one unit ahead,
+    // so that neither round trip delays the bulk copies of the current unit.
+    uint32_t u_next = 0, dead_next = 0;
+    if (lane == 0) u_next = atomicAdd(&hdr->ticket, 1u);
     while (!done) {
       uint32_t u = 0, dead = 0;
       if (lane == 0) {
-        u = atomicAdd(&hdr->ticket, 1u);
-        dead = aborted(hdr) ? 1u : 0u;
+        u = u_next;
+        dead = dead_next;
+        if (u < L.total_units && !dead) {
+          u_next = atomicAdd(&hdr->ticket, 1u);
+          dead_next = aborted(hdr) ? 1u : 0u;
+        }
       }
       u = __shfl_sync(FULL, u, 0);
       dead = __shfl_sync(FULL, dead, 0);
@@ -668,7 +696,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       acc_ptr = nullptr;
       acc_q = -1;
     }
-    if (end) break;
+    if (end) {
+      if (lane == 0) bulk_wait_all();  // bulk stores this warp issued have completed
+      break;
+    }
     const uint8_t *stage = stages + (size_t)s * kStageBytes;
     const uint32_t rows = mt.rows;
     const int ngroups = (int)((rows + kGroup - 1) / kGroup);
@@ -688,49 +719,80 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       return __shfl_sync(FULL, j, 0);
     };
     if (mt.dead == 0) {
-      if (mode == MODE_COUNT) {
-        for (int j = claim(); j < npairs; j = claim()) {
-          const int g = 2 * j, g1 = g + 1;
-          const int gs[2] = {g, g1 < ngroups ? g1 : g};
-          uint32_t m[2];
-          eval_groups<2>(Q, stage, gs, lane, m);
-          acc += __popc(m[0] & valid_mask(g, lane, rows));
-          if (g1 < ngroups) acc += __popc(m[1] & valid_mask(g1, lane, rows));
-        }
-      } else {  // MODE_BITMAP / MODE_SELECT: one bitmap word per 32 rows
-        const uint32_t nwords = (Q->nrows + 31u) / 32u;
-        uint32_t *bm = Q->bitmap;
-        uint32_t *gc = mode == MODE_SELECT ? Q->gcounts : nullptr;
-        for (int j = claim(); j < npairs; j = claim()) {
-          const int g = 2 * j, g1 = g + 1;
-          const int gs[2] = {g, g1 < ngroups ? g1 : g};
-          uint32_t mm[2];
-          eval_groups<2>(Q, stage, gs, lane, mm);
+      // one evaluation loop for every mode (a single inlined copy of the
+      // interpreter); the per-group epilogue branches on the mode (uniform)
+      const uint32_t nwords = (Q->nrows + 31u) / 32u;
+      uint32_t *bm = Q->bitmap;
+      uint32_t *rbm = reinterpret_cast<uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
+      for (int j = claim(); j < npairs; j = claim()) {
+        const int g = 2 * j, g1 = g + 1;
+        const int gs[2] = {g, g1 < ngroups ? g1 : g};
+        uint32_t mm[2];
+        eval_groups<2>(Q, stage, gs, lane, mm);
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            if (i == 1 && g1 >= ngroups) break;
-            const uint32_t m = mm[i] & valid_mask(gs[i], lane, rows);
-            const uint32_t c = __popc(m);
-            acc += c;
+        for (int i = 0; i < 2; ++i) {
+          if (i == 1 && g1 >= ngroups) break;
+          const uint32_t m = mm[i] & valid_mask(gs[i], lane, rows);
+          const uint32_t c = __popc(m);
+          acc += c;
+          if (mode == MODE_COUNT) continue;
+          uint32_t word = 0;
+          if (mode == MODE_SELECT) {
             uacc += c;
-            const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
-            if (gc) {
-              const uint32_t gcount = __reduce_add_sync(FULL, c);
-              if (lane == 0) gc[gidx] = gcount;
-              if (gcount == 0) continue;  // the write pass reads no bitmap word of an empty group
+            // selection bitmap in lane order: word p = the lanes' mask bit p,
+            // i.e. bit l of word p is row 64*(p/2) + 2*l + p%2 of the group
+            // (the write kernel counts a group's rows from its words)
+            uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+            if (__any_sync(FULL, m != 0u)) {
+              lo.x = __ballot_sync(FULL, m & 1u);
+              lo.y = __ballot_sync(FULL, m & 2u);
+              lo.z = __ballot_sync(FULL, m & 4u);
+              lo.w = __ballot_sync(FULL, m & 8u);
+              hi.x = __ballot_sync(FULL, m & 16u);
+              hi.y = __ballot_sync(FULL, m & 32u);
+              hi.z = __ballot_sync(FULL, m & 64u);
+              hi.w = __ballot_sync(FULL, m & 128u);
             }
-            uint32_t word = 0;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {  // words of rows 32p .. 32p+31 of the group
-              const int src = 16 * (p & 1) + (lane >> 1);
-              const int bit = 2 * (p >> 1) + (lane & 1);
-              const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
-              if (lane == p) word = bb;
+            if (lane == 0) {
+              uint4 *dst = reinterpret_cast<uint4 *>(rbm + gs[i] * 8);
+              dst[0] = lo;
+              dst[1] = hi;
             }
-            const uint32_t wi = gidx * 8u + (uint32_t)lane;
-            if (lane < 8 && wi < nwords) bm[wi] = word;
+            continue;
           }
+          const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {  // caller's bitmap: words of rows 32p .. 32p+31 of the group
+            const int src = 16 * (p & 1) + (lane >> 1);
+            const int bit = 2 * (p >> 1) + (lane & 1);
+            const uint32_t bb = __ballot_sync(FULL, (__shfl_sync(FULL, m, src) >> bit) & 1u);
+            if (lane == p) word = bb;
+          }
+          const uint32_t wi = gidx * 8u + (uint32_t)lane;
+          if (lane < 8 && wi < nwords) bm[wi] = word;
         }
+      }
+    }
+    if (mode == MODE_SELECT && mt.dead == 0) {
+      // the tile's last consumer writes its staged results with bulk copies
+      // and waits until they have read shared memory before releasing the stage
+      fence_proxy_async_smem();
+      __syncwarp();
+      uint32_t last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&resdone[s], 1u) == (uint32_t)kConsumers - 1u ? 1u : 0u;
+        __threadfence_block();
+      }
+      if (__shfl_sync(FULL, last, 0)) {
+        if (lane == 0) {
+          resdone[s] = 0;
+          const uint32_t ng = (uint32_t)ngroups;
+          const uint32_t *rb = reinterpret_cast<const uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
+          bulk_store(Q->bitmap + (size_t)mt.tile * Q->gmax * 8u, rb, ng * 32u);
+          bulk_commit_wait_read();
+        }
+        __syncwarp();
       }
     }
     if (mode != MODE_SELECT) retire_tile(Q->tiles_left, Q->done_ns, lane);
@@ -753,13 +815,17 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
 //     and never waits.
 //  2. Each group's first slot: a block-wide exclusive scan of the group
 //     counts of the unit.
-//  3. The unit's groups are split evenly over the warps (at most 32 each).  A dense group (at least
-//     kDenseMin qualifying rows, all 256 rows inside the table) takes the
-//     whole warp: 16-byte vector loads of the projected columns (lane l: rows
-//     8l .. 8l+7), staged in shared memory at their output slots, stored with
-//     lane = slot.  Every other group takes one lane, which walks its group's
-//     bitmap words in row order and stages (row, slot) entries; the warp then
-//     copies the staged entries, 4 per lane, loads before stores.
+//  3. The unit's groups are split evenly over the warps (at most 32 each).
+//     A dense group (at least kDenseMin qualifying rows, all 256 rows inside
+//     the table) takes the whole warp: its projected columns arrive in shared
+//     memory by asynchronous copies and each output slot takes its row's
+//     value from there, so that stores coalesce.  Every other group takes one
+//     lane, which walks its group's rows in order and stages (row, slot)
+//     entries; the warp then copies the staged entries, 4 per lane, loads
+//     before stores.
+// The selection bitmap is in lane order (see the scan kernel): bit l of the
+// group's word p is its row 64*(p/2) + 2*l + p%2, so row order within a block
+// of 64 rows merges an even-row word and an odd-row word.
 
 constexpr int kWriteThreads = 256;
 constexpr int kWriteWarps = kWriteThreads / 32;
@@ -817,7 +883,6 @@ struct GatherInfo {
   uint64_t capacity;
   uint32_t *out_ids;
   const uint32_t *bitmap;
-  const uint32_t *gcounts;
   const unsigned long long *goff;
   unsigned int *tiles_left;
   unsigned long long *done_ns;
@@ -868,6 +933,12 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
   }
 }
 
+// Bits 0..3 of x to bits 0, 2, 4, 6.
+__device__ __forceinline__ uint32_t spread4(uint32_t x) {
+  x = (x | (x << 2)) & 0x33u;
+  return (x | (x << 1)) & 0x55u;
+}
+
 // One dense group, the whole warp.  The projected columns of all 256 rows
 // arrive together (16-byte asynchronous copies, at most kRawBytes at a
 // time; a column wider than that is read in place); each output slot then
@@ -875,7 +946,10 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
 __device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &W, int j, uint32_t g, uint32_t cnt,
                                             unsigned long long base, int lane) {
   const uint64_t cap = G.capacity;
-  const uint32_t bits8 = (W.words[j][lane >> 2] >> (8 * (lane & 3))) & 0xffu;
+  // rows 8l .. 8l+7 of the group: bits 4(l%8) .. 4(l%8)+3 of the even-row
+  // and odd-row words of block l/8 (lane-order bitmap), interleaved
+  const uint32_t jj = (uint32_t)lane >> 3, sub = 4u * ((uint32_t)lane & 7u);
+  const uint32_t bits8 = spread4((W.words[j][2 * jj] >> sub) & 0xfu) | (spread4((W.words[j][2 * jj + 1] >> sub) & 0xfu) << 1);
   const uint32_t cl = __popc(bits8);
   uint32_t incl = cl;
 #pragma unroll
@@ -944,7 +1018,6 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
       G.capacity = Q->capacity;
       G.out_ids = Q->out_ids;
       G.bitmap = Q->bitmap;
-      G.gcounts = Q->gcounts;
       G.tiles_left = Q->tiles_left;
       G.done_ns = Q->done_ns;
       G.ngroups = Q->ngroups;
@@ -968,16 +1041,16 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   const int gi = warp * gpw + lane;
   const bool valid = lane < gpw && gi < ng;
   const uint32_t grp_l = g0 + (uint32_t)gi;
-  // the group's count and bitmap words in one round trip (the scan wrote the
-  // words of every group with a qualifying row; the others are never used)
-  uint32_t c = 0;
+  // the group's bitmap words (the scan wrote all 8 words of every group) and
+  // its count
   uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
   if (valid) {
     const uint4 *bw = reinterpret_cast<const uint4 *>(Q->bitmap + (size_t)grp_l * 8);
-    c = Q->gcounts[grp_l];
     wlo = __ldcg(bw);
     whi = __ldcg(bw + 1);
   }
+  const uint32_t c = __popc(wlo.x) + __popc(wlo.y) + __popc(wlo.z) + __popc(wlo.w) + __popc(whi.x) +
+                     __popc(whi.y) + __popc(whi.z) + __popc(whi.w);
   uint32_t inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1066,12 +1139,26 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
           // the group's first sc set bits are its rows: never read past sc
           const uint32_t eend = min(wend, sx + sc);
           uint32_t e = sx;  // staged index of this lane's next entry
+          // rows in order: within block j (rows 64j .. 64j+63), merge the
+          // even-row word 2j and the odd-row word 2j+1 of the lane-order bitmap
 #pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const uint4 &h = p < 4 ? wlo : whi;
-            const uint32_t wp = (p & 3) == 0 ? h.x : (p & 3) == 1 ? h.y : (p & 3) == 2 ? h.z : h.w;
-            for (uint32_t x = wp; x != 0 && e < eend; x &= x - 1, ++e)
-              if (e >= win) ent[e - win] = ((rrel + 32u * p + (uint32_t)(__ffs(x) - 1)) << 16) | (srel + e - sx);
+          for (int jb = 0; jb < 4; ++jb) {
+            const uint4 &h = jb < 2 ? wlo : whi;
+            uint32_t ev = (jb & 1) ? h.z : h.x, od = (jb & 1) ? h.w : h.y;
+            while ((ev | od) != 0u && e < eend) {
+              const uint32_t pe = ev ? (uint32_t)__ffs(ev) - 1u : 32u;
+              const uint32_t po = od ? (uint32_t)__ffs(od) - 1u : 32u;
+              uint32_t rr;
+              if (pe <= po) {
+                rr = 2u * pe;
+                ev &= ev - 1u;
+              } else {
+                rr = 2u * po + 1u;
+                od &= od - 1u;
+              }
+              if (e >= win) ent[e - win] = ((rrel + 64u * jb + rr) << 16) | (srel + e - sx);
+              ++e;
+            }
           }
         }
         __syncwarp();
@@ -1231,14 +1318,12 @@ esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) 
 size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
 size_t select_other_bytes(const Query &q) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
-  return ((groups * 32 + 255) & ~(size_t)255) + ((groups * 4 + 255) & ~(size_t)255);
+  return (groups * 32 + 255) & ~(size_t)255;
 }
 void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   q.unit_total = reinterpret_cast<unsigned long long *>(zeroed);
   q.unit_status = q.unit_total + q.nunits;
-  const size_t groups = (size_t)q.ntiles * q.gmax;
   q.bitmap = reinterpret_cast<uint32_t *>(other);
-  q.gcounts = reinterpret_cast<uint32_t *>(other + ((groups * 32 + 255) & ~(size_t)255));
 }
 
 // Validates a (table, pred, rows) call and fills the per-call query.

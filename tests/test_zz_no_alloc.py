@@ -54,7 +54,7 @@ def test_noalloc_matches_selectivity_twice(esc):
 
 def test_noalloc_limits(esc):
     # counting needs no per-row scratch: any size works
-    t = datagen.single_table(100_000_000, seed=1, device="cuda")
+    t = datagen.single_table(130_000_000, seed=1, device="cuda")
     tbl = esc.Table.from_datagen(t)
     p = esc.Predicate(tbl, "category = 3 AND day < 100", ("key",))
     assert esc.esc_selectivity_noalloc(tbl.handle, p.handle)[0] == esc.count(tbl, p)
