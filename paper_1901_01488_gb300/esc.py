@@ -279,7 +279,7 @@ def esc_semijoin_counts(fact: int, fk_cols: Sequence[str], bitmaps: Sequence[tor
                         dim_rows: Sequence[int], stream=None) -> List[int]:
     nd = len(fk_cols)
     names = (ctypes.c_char_p * nd)(*[c.encode() for c in fk_cols])
-    bms = (_P * nd)(*[b.data_ptr() for b in bitmaps])
+    bms = (_P * nd)(*[b.data_ptr() if b is not None else None for b in bitmaps])
     rows = (ctypes.c_uint64 * nd)(*dim_rows)
     out = (ctypes.c_uint64 * (1 << nd))()
     _check(_lib.esc_semijoin_counts(fact, names, nd, bms, rows, out, _stream(stream)), "esc_semijoin_counts")

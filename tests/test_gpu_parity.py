@@ -199,6 +199,33 @@ def test_bitmap_and_semijoin(esc):
     assert got2 == [exp2[s] for s in range(4)]
 
 
+def test_semijoin_edges(esc):
+    """Keys outside [0, rows) (negative, past the end, the int32 extremes), a
+    dimension with no rows, one too large for shared memory (probed in
+    place), and bitmaps whose bits past the last row are set."""
+    rng = np.random.default_rng(8)
+    n = 200_003
+    dims_rows = [0, 37, 1_000_000, 70]
+    fk, marks, bms = [], [], []
+    for d, rows in enumerate(dims_rows):
+        k = rng.integers(-40, rows + 40, n).astype(np.int32)
+        k[rng.integers(0, n, 50)] = np.iinfo(np.int32).min
+        k[rng.integers(0, n, 50)] = np.iinfo(np.int32).max
+        fk.append(k)
+        words = (rows + 31) // 32
+        w = rng.integers(0, 2**32, max(words, 1), dtype=np.uint64).astype(np.uint32)  # garbage past `rows` too
+        bits = np.unpackbits(w.view(np.uint8), bitorder="little")[:rows]
+        marks.append(bits.astype(np.uint8))
+        bms.append(torch.from_numpy(w.view(np.int32).copy()).cuda() if words else None)
+    cols = [(f"fk{d}", "i32", torch.from_numpy(fk[d]).cuda()) for d in range(4)]
+    tbl = esc.Table(cols, n)
+    for sel in ([0, 1, 2, 3], [2, 0], [3], [1, 2]):
+        got = esc.esc_semijoin_counts(tbl.handle, [f"fk{d}" for d in sel], [bms[d] for d in sel],
+                                      [dims_rows[d] for d in sel])
+        exp = oracle.semijoin_counts([fk[d] for d in sel], [marks[d] for d in sel], list(range(1 << len(sel))))
+        assert got == [exp[s] for s in range(1 << len(sel))], sel
+
+
 def test_empty_table(esc):
     x = torch.zeros(16, dtype=torch.int32, device="cuda")
     tbl = esc.Table([("a", "i32", x)], 0)
