@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -64,10 +65,14 @@ def measured_peak_hbm():
 
 
 def source_digest() -> str:
+    """Digest of the scan and write kernels' code: comments removed and
+    whitespace collapsed, so that a comment edit keeps a profile valid."""
     h = hashlib.sha256()
     for p in ("paper_1901_01488_gb300/csrc/esc_scan.cu", "paper_1901_01488_gb300/csrc/esc_internal.h"):
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            code = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,25 +5,26 @@
 // counts of esc_semijoin.cu).
 //
 // Kernel shape (sm_103a):
-//  * persistent: one CTA per SM, 1 producer warp + kConsumers consumer warps;
-//  * tiles of a few thousand rows are claimed in order from a global ticket,
-//    so a tile's predecessors are always owned by running CTAs (the look-back
-//    below can never wait on a CTA that is not resident);
+//  * scan_kernel, persistent: one CTA per SM, 1 producer warp + kConsumers
+//    consumer warps; work units (a few consecutive tiles) are claimed in
+//    order from a global ticket;
 //  * the producer stages every column the predicate reads into shared memory
 //    with 1-D bulk TMA copies (cp.async.bulk ... mbarrier::complete_tx) into a
 //    ring of kStages stages; the ragged tail of the last tile (< 16 bytes per
 //    column) is copied with plain loads;
-//  * consumers interpret the postfix program on 8 rows per lane, keeping the
+//  * consumers claim pairs of 256-row groups of a stage from a shared counter
+//    and interpret the postfix program on 8 rows per lane, keeping the
 //    boolean evaluation stack as 8-bit masks in one 64-bit register;
-//  * counts: popc + warp reduction + one atomic per warp and tile;
-//  * ordered compaction: per-group counts -> per-tile exclusive scan ->
-//    decoupled look-back across tiles (Merrill & Garland, "Single-pass
-//    Parallel Prefix Scan with Decoupled Look-back", 2016) -> each warp
-//    re-walks its groups 32 consecutive rows at a time (lane = row, one
-//    __ballot_sync per 32 rows) and writes ids and projected values to
+//  * counts: popc per lane, one atomic per warp and query;
+//  * ordered compaction, first pass: the selection bitmap (lane order),
+//    staged per tile in shared memory and written with one bulk copy, and a
+//    total per work unit; second pass (write_kernel, one block per unit): a
+//    decoupled look-back over the unit totals (Merrill & Garland,
+//    "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), a
+//    block scan of the group counts, then ids and projected values to
 //    consecutive output slots.
-// Every wait (mbarrier, look-back) is bounded by %globaltimer; on expiry the
-// kernel records ESC_ETIMEOUT in the scratch header and all CTAs wind down.
+// Every wait on an mbarrier is bounded by %globaltimer; on expiry the kernel
+// records ESC_ETIMEOUT in the scratch header and all CTAs wind down.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -543,7 +544,8 @@ struct SmemLayout {
 
 // ------------------------------------------------------------------ the scan kernel
 // Warp 0: producer (unit tickets, bulk copies).  Warps 1..: consumers
-// (evaluate; count; write bitmap words, group counts and unit totals).
+// (evaluate; count; compaction: bitmap words and unit totals; bitmap mode:
+// the caller's bitmap words).
 __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *stages = smem + SmemLayout::stages;
@@ -1312,9 +1314,8 @@ esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) 
 }
 
 // Compaction scratch of one query: unit totals and look-back words (both
-// zeroed before the scan), then the selection bitmap and group counts (the
-// scan writes every group count, and the bitmap words of every group with a
-// qualifying row, before the write kernel reads them).
+// zeroed before the scan), then the selection bitmap (the scan writes every
+// word before the write kernel reads it).
 size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
 size_t select_other_bytes(const Query &q) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
@@ -1376,7 +1377,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.nq = 1;
   L.total_units = L.q0.nunits;
   // scratch: header + count, then (compaction) unit totals and look-back
-  // words (zeroed with the header), then the selection bitmap and group counts
+  // words (zeroed with the header), then the selection bitmap
   const size_t head = (sizeof(SingleScratch) + 255) & ~(size_t)255;
   const size_t zeroed = mode == MODE_SELECT ? select_zeroed_bytes(L.q0) : 0;
   const size_t other = mode == MODE_SELECT ? select_other_bytes(L.q0) : 0;
@@ -1536,7 +1537,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   b->write_blocks = (uint32_t)wunits;
   // device memory: queries | zeroed every run: header, counts, done times,
   // countdowns, unit totals + look-back words | countdown initial values |
-  // selection bitmaps + group counts
+  // selection bitmaps
   const size_t q_span = (sizeof(Query) * (size_t)n + 255) & ~(size_t)255;
   const size_t hdr_bytes = 256;
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
@@ -1774,7 +1775,7 @@ esc_status esc_selftest_wait_timeout(uint64_t limit_ns, void *stream) {
 // ------------------------------------------------------------------ allocation-free variant
 // esc_selectivity_noalloc: the same sub-query for callers that must not
 // allocate device memory.  Its scratch (launch header, count, unit words,
-// selection bitmap, group counts) is one array in this library's device
+// selection bitmap) is one array in this library's device
 // image, sized kNoAllocScratchBytes; the CUDA driver reserves it on every
 // device where the library's kernels are loaded, until the process exits.
 

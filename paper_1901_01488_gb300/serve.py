@@ -36,10 +36,11 @@ class Request:
 
 def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
     """Device memory a request holds while in flight: library scratch for
-    materialisation (~0.17 B/row) and its output buffers."""
+    materialisation (the selection bitmap, 1/8 byte per row, and 16 bytes
+    per work unit of at least 2048 rows) and its output buffers."""
     if not req.proj:
         return 256
-    scratch = nrows * 44 // 256 + 4096
+    scratch = nrows // 8 + nrows // 128 + 4096
     return scratch + req.capacity * (4 + sum(widths[c] for c in req.proj))
 
 
