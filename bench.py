@@ -52,8 +52,8 @@ def parse_args():
 
 
 def env_rank():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1901_01488_gb300.replicas import env_rank as er
+    return er()
 
 
 def measured_peak_hbm():
@@ -205,7 +205,8 @@ def run_esc(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    t = datagen.skewed_table(args.rows, seed=2 + rank, device=dev)
+    from paper_1901_01488_gb300 import replicas
+    t = datagen.skewed_table(args.rows, seed=replicas.table_seed(rank), device=dev)
     table = esc.Table.from_datagen(t)
     ptexts = datagen.skewed_predicates(args.preds)
     proj = datagen.SKEWED_PROJECTION
@@ -245,11 +246,7 @@ def run_esc(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        x = torch.tensor([ms], device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms = float(x.item())
+    ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     assert dev_counts.tolist() == counts, "counts changed between runs"
     per_q = [[ev[k][j][0].elapsed_time(ev[k][j][1]) for j in range(len(preds))] for k in range(K)]
     lat = sorted(x for row in per_q for x in row)
@@ -258,8 +255,7 @@ def run_esc(args):
     kern_s = sum(sum(row) for row in per_q) / 1e3
     achieved = sum(alg) * K / kern_s / 1e9
     peak, peak_src = measured_peak_hbm()
-    rows_total = args.rows * len(preds) * K * world
-    value = rows_total / (ms / 1e3)
+    value = replicas.job_value(args.rows * len(preds) * K, world, ms)
     step_gbs = sum(alg) * K * world / (ms / 1e3) / 1e9
 
     # end to end through the C ABI with host buffers: H2D of the columns, the
