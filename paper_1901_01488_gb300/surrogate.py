@@ -87,13 +87,18 @@ def qerror(est: np.ndarray, true: np.ndarray) -> np.ndarray:
     return np.maximum(e / t, t / e)
 
 
-def exact_counts(esc, table, preds: Sequence[datagen.Predicate], chunk: int = 2048) -> np.ndarray:
-    """Exact ESC counts of many predicates on one table (batched launches)."""
-    out = np.zeros(len(preds), dtype=np.int64)
-    for s in range(0, len(preds), chunk):
+def exact_counts(esc, table, preds: Sequence[datagen.Predicate], chunk: int = 2048, stream=None) -> np.ndarray:
+    """Exact ESC counts of many predicates on one table: one batched launch per
+    chunk (esc_selectivity_batch_async), counts read back once at the end."""
+    n = len(preds)
+    dev = torch.zeros(max(1, n), dtype=torch.int64, device="cuda")
+    keep = []
+    for s in range(0, n, chunk):
         ps = [esc.Predicate(table, p.text) for p in preds[s:s + chunk]]
-        counts, _ = esc.esc_selectivity_batch([table.handle] * len(ps), [p.handle for p in ps])
-        out[s:s + len(ps)] = counts
+        esc.esc_selectivity_batch_async([table.handle] * len(ps), [p.handle for p in ps], dev[s:s + len(ps)],
+                                        stream=stream)
+        keep.append(ps)  # predicates stay alive until their launch has run
+    out = dev[:n].cpu().numpy().astype(np.int64)
     return out
 
 
