@@ -105,6 +105,11 @@ uint64_t esc_table_nrows(const esc_table *table);
  *   operand := column | udf '(' column ',' column ',' INT ')'
  *   cmp     := = | == | != | <> | < | <= | > | >=
  * INT is a decimal int64.  BETWEEN is inclusive (empty when lo > hi).
+ * The compiled program is an exact simplification: comparisons become ranges
+ * clamped to the operand's domain, and tests on one operand (a column, or a
+ * udf with the same columns in either order and the same m) combine --
+ * intersected under AND, united under OR -- so esc_predicate_explain may
+ * list fewer tests than the text has; results never change.
  * udf(a, b, m) is (a * b) mod m with the product wrapping in 64-bit two's
  * complement and the remainder truncated toward zero; m must be > 0.
  * An IN list holds at most 16 values; an empty list is false.
@@ -200,7 +205,7 @@ esc_status esc_batch_destroy(esc_batch *batch);
 
 /* Asynchronous batch without a prepared graph, for a stream of changing
  * sub-queries (the serving loop): enqueues the n sub-queries as one
- * persistent scan launch (plus the two compaction launches when any has
+ * persistent scan launch (plus one compaction write launch when any has
  * rows), with scratch from the library's stream-ordered pool.  Writes n exact
  * counts to dev_counts and, when dev_done_ns is not NULL, each sub-query's
  * completion time (%globaltimer).  Does not synchronise; `rows` entries with
