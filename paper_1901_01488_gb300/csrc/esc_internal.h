@@ -88,9 +88,8 @@ struct Query {
   uint8_t ref_w[kMaxRef];         // element width of each read column
   uint8_t proj_w[kMaxProj];
   int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
-  uint32_t pad0;
   uint32_t ngroups;       // 256-row groups: ceil(nrows / 256)
-  uint32_t pad1[2];
+  uint32_t pad1[3];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];
@@ -98,8 +97,6 @@ struct Query {
   uint32_t *bitmap;               // MODE_BITMAP: caller's bitmap; MODE_SELECT: selection bitmap scratch
   uint64_t capacity;
   unsigned long long *count;      // exact count accumulates here (zeroed before launch)
-  void *pad3;
-  void *pad2;
   unsigned long long *unit_total; // MODE_SELECT: qualifying rows per unit (zeroed)
   unsigned long long *unit_status;// write kernel's decoupled look-back words, one per unit (zeroed)
   unsigned int *tiles_left;       // completion countdown (set before launch; see the kernels)

@@ -831,6 +831,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
 
 constexpr int kWriteThreads = 256;
 constexpr int kWriteWarps = kWriteThreads / 32;
+static_assert(kMaxUnitGroups <= kWriteThreads, "one write-kernel thread per group of a unit");
 constexpr uint32_t kDenseMin = 97;       // qualifying rows of a group for the dense path
 constexpr uint32_t kRawBytes = 2048;     // per warp: a dense group's projected values (<= 8 B per row at once)
 constexpr uint32_t kStageEntries = kRawBytes / 4;  // sparse entries staged per warp (same buffer)
@@ -1179,6 +1180,31 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   }
 }
 
+// A program that reads no column is a constant (the compiler folded it:
+// e.g. a conjunction of contradictory tests): its result needs no scan.
+// Writes the count, and for a constant TRUE the caller's bitmap words or the
+// materialised rows (ids 0.., projected columns copied); FALSE leaves rows
+// unwritten and the bitmap zero.
+__global__ void __launch_bounds__(256) const_kernel(const __grid_constant__ Launch L, uint32_t value) {
+  const Query &q = L.q0;
+  const uint64_t n = value ? q.nrows : 0u;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (tid == 0) *q.count = n;
+  if (q.mode == MODE_BITMAP) {
+    const uint32_t nwords = (q.nrows + 31u) / 32u, tail = q.nrows & 31u;
+    for (uint64_t w = tid; w < nwords; w += stride)
+      q.bitmap[w] = !value ? 0u : (w + 1 == nwords && tail) ? (1u << tail) - 1u : ~0u;
+  } else if (q.mode == MODE_SELECT && value) {
+    const uint64_t m = min(n, (uint64_t)q.capacity);
+    for (uint64_t i = tid; i < m; i += stride) {
+      q.out_ids[i] = (uint32_t)i;
+      for (int c = 0; c < q.nproj; ++c)
+        store_elem(q.out_proj[c], i, load_elem(q.proj_ptr[c], (uint32_t)i, q.proj_w[c]), q.proj_w[c]);
+    }
+  }
+}
+
 // A kernel whose only job is a bounded wait on a flag that nothing sets.
 __global__ void wait_selftest_kernel(const unsigned *flag, ScratchHdr *hdr, uint64_t limit_ns) {
   const uint64_t t0 = globaltimer();
@@ -1244,6 +1270,54 @@ esc_status device_state(DeviceState **out) {
 
 // Tile size for a query: as many rows as fit in one stage, a multiple of the
 // 256-row group, at most kMaxTileRows.
+// The value of a program that reads no column (TRUE, FALSE and connectives
+// only); false when the program reads a column.
+bool program_constant(const Query &q, uint32_t *value) {
+  if (q.nref != 0) return false;
+  uint8_t stack[kMaxDepth + 1];
+  int sp = 0;
+  for (int pc = 0; pc < q.ninstr; ++pc) {
+    switch (q.code[pc].op) {
+      case OP_TRUE:
+      case OP_FALSE:
+        if (sp > kMaxDepth) return false;
+        stack[sp++] = q.code[pc].op == OP_TRUE ? 1 : 0;
+        break;
+      case OP_NOT:
+        if (sp < 1) return false;
+        stack[sp - 1] ^= 1;
+        break;
+      case OP_AND:
+      case OP_OR:
+        if (sp < 2) return false;
+        --sp;
+        stack[sp - 1] = q.code[pc].op == OP_AND ? (stack[sp - 1] & stack[sp]) : (stack[sp - 1] | stack[sp]);
+        break;
+      case OP_JZ:
+      case OP_JNZ:
+        break;  // a jump only skips work whose result is already decided
+      default:
+        return false;
+    }
+  }
+  if (sp != 1) return false;
+  *value = stack[0];
+  return true;
+}
+
+esc_status launch_const(const Launch &L, uint32_t value, cudaStream_t st) {
+  DeviceState *d;
+  esc_status s = device_state(&d);
+  if (s != ESC_OK) return s;
+  const Query &q = L.q0;
+  const uint64_t work = q.mode == MODE_BITMAP ? (q.nrows + 31u) / 32u
+                        : (q.mode == MODE_SELECT && value) ? std::min<uint64_t>(q.nrows, q.capacity) : 0;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d->sms * 8, (work + 255) / 256));
+  const_kernel<<<grid, 256, 0, st>>>(L, value);
+  ESC_CK(cudaGetLastError());
+  return ESC_OK;
+}
+
 uint32_t tile_rows_for(const Query &q, const esc_tuning &tu) {
   uint32_t bpr = 0;
   for (int i = 0; i < q.nref; ++i) bpr += q.ref_w[i];
@@ -1394,8 +1468,13 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   L.hdr = &sc->hdr;
   L.q0.count = dev_count ? dev_count : &sc->count;
   if (mode == MODE_SELECT) select_bind(L.q0, base + head, base + head + zeroed);
-  s = launch_scan(L, st);
-  if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
+  uint32_t cval = 0;
+  if (program_constant(L.q0, &cval)) {
+    s = launch_const(L, cval, st);
+  } else {
+    s = launch_scan(L, st);
+    if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
+  }
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
     return s;
@@ -1874,7 +1953,11 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
   L.hdr = &h->hdr;
   q.count = &h->count;
   if (mode == MODE_SELECT) select_bind(q, d->scratch + head, d->scratch + head + zeroed);
-  if (L.total_units > 0) {
+  uint32_t cval = 0;
+  if (program_constant(q, &cval)) {
+    esc_status cs = launch_const(L, cval, st);
+    if (cs != ESC_OK) return cs;
+  } else if (L.total_units > 0) {
     const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), L.total_units);
     scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());

@@ -91,6 +91,34 @@ def test_truncation(esc):
     assert st0 == esc.ESC_ETRUNC and cnt0 == len(exp_ids)
 
 
+def test_constant_programs(esc):
+    """Predicates that fold to TRUE or FALSE (no column read) take no scan:
+    counts, rows, truncation, bitmaps and the allocation-free entry point."""
+    n = 5_003
+    cols = host_table(n, seed=9)
+    tbl = esc.Table(as_columns(cols, "cuda"), n)
+    cases = [("TRUE", n), ("FALSE", 0), ("b = 1 AND b = 2", 0), ("b < 100 OR b >= 50", n),
+             ("NOT (a = 1 AND a = 2)", n), ("udf(c, a, 7) > 6", 0), ("d BETWEEN 70000 AND 80000 OR TRUE", n)]
+    for text, exp in cases:
+        p = esc.Predicate(tbl, text, ("c", "b"))
+        assert not any(l.startswith("ref ") for l in p.explain().splitlines()), text
+        assert esc.count(tbl, p) == exp == oracle.count(text, cols), text
+        ids_o, proj_o = oracle.select(text, cols, ("c", "b"))
+        cnt, ids, proj = esc.select(tbl, p)
+        assert cnt == exp and np.array_equal(ids.cpu().numpy().view(np.uint32), ids_o), text
+        assert np.array_equal(proj[0].cpu().numpy(), proj_o["c"]) and np.array_equal(proj[1].cpu().numpy(), proj_o["b"])
+        rows = p.alloc_rows(100)
+        c2, st = esc.esc_selectivity(tbl.handle, p.handle, rows)
+        assert c2 == exp and st == (esc.ESC_ETRUNC if exp > 100 else esc.ESC_OK)
+        assert np.array_equal(rows[1].cpu().numpy().view(np.uint32)[:min(exp, 100)], ids_o[:100])
+        c3, _ = esc.esc_selectivity_noalloc(tbl.handle, p.handle, p.alloc_rows(n))
+        assert c3 == exp
+        bm = torch.full(((n + 31) // 32,), -1, dtype=torch.int32, device="cuda")
+        assert esc.esc_bitmap_build(tbl.handle, p.handle, bm) == exp
+        bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")
+        assert bits[:n].sum() == exp and bits[n:].sum() == 0, text     # tail bits clear
+
+
 def test_skewed_table_2m(esc):
     t = datagen.skewed_table(2_000_000, seed=2, device="cuda")
     host = t.host()
