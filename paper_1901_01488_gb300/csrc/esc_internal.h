@@ -89,7 +89,9 @@ struct Query {
   uint8_t proj_w[kMaxProj];
   int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
   uint32_t ngroups;       // 256-row groups: ceil(nrows / 256)
-  uint32_t pad1[3];
+  uint32_t is_const;      // the program reads no column: no work units, answered by the constant kernel
+  uint32_t const_value;   // its value (0 or 1) when is_const
+  uint32_t pad1;
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

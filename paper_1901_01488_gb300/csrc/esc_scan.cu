@@ -1185,11 +1185,8 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
 // Writes the count, and for a constant TRUE the caller's bitmap words or the
 // materialised rows (ids 0.., projected columns copied); FALSE leaves rows
 // unwritten and the bitmap zero.
-__global__ void __launch_bounds__(256) const_kernel(const __grid_constant__ Launch L, uint32_t value) {
-  const Query &q = L.q0;
+__device__ __forceinline__ void const_body(const Query &q, uint32_t value, uint64_t tid, uint64_t stride) {
   const uint64_t n = value ? q.nrows : 0u;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   if (tid == 0) *q.count = n;
   if (q.mode == MODE_BITMAP) {
     const uint32_t nwords = (q.nrows + 31u) / 32u, tail = q.nrows & 31u;
@@ -1201,6 +1198,26 @@ __global__ void __launch_bounds__(256) const_kernel(const __grid_constant__ Laun
       q.out_ids[i] = (uint32_t)i;
       for (int c = 0; c < q.nproj; ++c)
         store_elem(q.out_proj[c], i, load_elem(q.proj_ptr[c], (uint32_t)i, q.proj_w[c]), q.proj_w[c]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) const_kernel(const __grid_constant__ Launch L, uint32_t value) {
+  const_body(L.q0, value, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+// The constant sub-queries of a batch: blockIdx.y indexes cidx (the batch's
+// constant queries), kConstBlocks blocks each; the last block of a query
+// records its completion time.
+constexpr int kConstBlocks = 32;
+__global__ void __launch_bounds__(256) const_batch_kernel(const Query *queries, const uint32_t *cidx, uint32_t y0) {
+  const Query &q = queries[cidx[y0 + blockIdx.y]];
+  const_body(q, q.const_value, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+  if (q.done_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicSub(q.tiles_left, 1u) == 1u) *q.done_ns = globaltimer();
     }
   }
 }
@@ -1303,6 +1320,26 @@ bool program_constant(const Query &q, uint32_t *value) {
   if (sp != 1) return false;
   *value = stack[0];
   return true;
+}
+
+// Batch builders: a query whose program is constant gets no work units (the
+// scan and write kernels skip it) and is answered by const_batch_kernel.
+void mark_constant(Query &q) {
+  uint32_t v = 0;
+  if (!program_constant(q, &v)) return;
+  q.is_const = 1;
+  q.const_value = v;
+  q.nunits = 0;
+  q.ntiles = 0;
+}
+
+esc_status launch_const_batch(const Query *dev_queries, const uint32_t *dev_cidx, uint32_t nconst, cudaStream_t st) {
+  for (uint32_t y0 = 0; y0 < nconst; y0 += 65535u) {
+    const dim3 grid(kConstBlocks, std::min<uint32_t>(65535u, nconst - y0));
+    const_batch_kernel<<<grid, 256, 0, st>>>(dev_queries, dev_cidx, y0);
+    ESC_CK(cudaGetLastError());
+  }
+  return ESC_OK;
 }
 
 esc_status launch_const(const Launch &L, uint32_t value, cudaStream_t st) {
@@ -1591,6 +1628,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   std::vector<Query> qs((size_t)n);
+  std::vector<uint32_t> cidx;
   uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
@@ -1598,6 +1636,8 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
                            &qs[i])) != ESC_OK)
       return s;
+    mark_constant(qs[i]);
+    if (qs[i].is_const) cidx.push_back((uint32_t)i);
     qs[i].unit_base = (uint32_t)units;
     qs[i].wunit_base = (uint32_t)wunits;
     units += qs[i].nunits;
@@ -1617,7 +1657,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   // device memory: queries | zeroed every run: header, counts, done times,
   // countdowns, unit totals + look-back words | countdown initial values |
   // selection bitmaps
-  const size_t q_span = (sizeof(Query) * (size_t)n + 255) & ~(size_t)255;
+  const size_t q_span = (sizeof(Query) * (size_t)n + 4 * (size_t)n + 255) & ~(size_t)255;  // queries + cidx
   const size_t hdr_bytes = 256;
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
@@ -1642,7 +1682,9 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     qs[i].count = &b->counts[i];
     qs[i].done_ns = &b->done[i];
     qs[i].tiles_left = &b->tiles_left[i];
-    if (qs[i].mode == MODE_SELECT) {
+    if (qs[i].is_const) {
+      init[i] = kConstBlocks;                         // counted down by the constant kernel
+    } else if (qs[i].mode == MODE_SELECT) {
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
@@ -1655,7 +1697,10 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     batch_free(b);
     return fail(ESC_EINVAL, "esc_batch_prepare: internal layout error");
   }
+  uint32_t *dev_cidx = reinterpret_cast<uint32_t *>(base + sizeof(Query) * (size_t)n);
   e = cudaMemcpy(b->queries, qs.data(), sizeof(Query) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !cidx.empty())
+    e = cudaMemcpy(dev_cidx, cidx.data(), 4 * cidx.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->tiles_init, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     batch_free(b);
@@ -1679,7 +1724,8 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
-    ls = launch_scan(L, cs);
+    if (!cidx.empty()) ls = launch_const_batch(b->queries, dev_cidx, (uint32_t)cidx.size(), cs);
+    if (ls == ESC_OK) ls = launch_scan(L, cs);
     if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
@@ -1749,6 +1795,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   if (n < 1 || !tables || !preds || !dev_counts)
     return fail(ESC_EINVAL, "esc_selectivity_batch_async: need n >= 1 tables, predicates and dev_counts");
   std::vector<Query> qs((size_t)n);
+  std::vector<uint32_t> cidx;
   uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
   esc_status s;
   for (int i = 0; i < n; ++i) {
@@ -1757,6 +1804,8 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
                            &qs[i])) != ESC_OK)
       return s;
+    mark_constant(qs[i]);
+    if (qs[i].is_const) cidx.push_back((uint32_t)i);
     qs[i].unit_base = (uint32_t)units;
     qs[i].wunit_base = (uint32_t)wunits;
     units += qs[i].nunits;
@@ -1768,7 +1817,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
     if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_selectivity_batch_async: too many work units");
   }
   // device block: queries | zeroed: header, counts, done, countdowns, unit words | bitmaps, group data
-  const size_t q_span = (sizeof(Query) * (size_t)n + 255) & ~(size_t)255;
+  const size_t q_span = (sizeof(Query) * (size_t)n + 4 * (size_t)n + 255) & ~(size_t)255;  // queries + cidx
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
   const size_t zbytes = 256 + 2 * cnt_bytes + left_bytes + (size_t)zeroed;
@@ -1787,7 +1836,9 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
     qs[i].count = &counts[i];
     qs[i].done_ns = dev_done_ns ? &done[i] : nullptr;
     qs[i].tiles_left = &left[i];
-    if (qs[i].mode == MODE_SELECT) {
+    if (qs[i].is_const) {
+      init[i] = kConstBlocks;
+    } else if (qs[i].mode == MODE_SELECT) {
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
@@ -1796,8 +1847,11 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       init[i] = qs[i].ntiles * (unsigned)kConsumers;
     }
   }
+  uint32_t *dev_cidx = reinterpret_cast<uint32_t *>(base + sizeof(Query) * (size_t)n);
   cudaError_t e = cudaMemsetAsync(z, 0, zbytes, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base, qs.data(), sizeof(Query) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !cidx.empty())
+    e = cudaMemcpyAsync(dev_cidx, cidx.data(), 4 * cidx.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && dev_done_ns)
     e = cudaMemcpyAsync(left, init.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
@@ -1810,7 +1864,8 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   L.nq = n;
   L.total_units = (uint32_t)units;
   L.hdr = reinterpret_cast<ScratchHdr *>(z);
-  s = launch_scan(L, st);
+  s = cidx.empty() ? ESC_OK : launch_const_batch(L.queries, dev_cidx, (uint32_t)cidx.size(), st);
+  if (s == ESC_OK) s = launch_scan(L, st);
   if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, st);
   if (s == ESC_OK) {
     e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);

@@ -196,6 +196,44 @@ def test_batch_matches_single(esc):
     esc.esc_batch_destroy(b)
 
 
+def test_batch_with_constant_programs(esc):
+    """Batches mixing constant programs (no work units; the constant kernel
+    answers them, TRUE with every row) with scanned ones: counts, rows and
+    completion times, prepared, one-shot and asynchronous."""
+    t = datagen.skewed_table(300_007, seed=31, device="cuda")
+    tbl = esc.Table.from_datagen(t)
+    host = t.host()
+    proj = datagen.SKEWED_PROJECTION
+    texts = ["FALSE", "day < 100", "code7 = 1 AND code7 = 2", "TRUE", "price > 9000000",
+             "qty < 5 OR qty >= 5", "key IN (1, 2, 3) AND key = 9", "day BETWEEN 5 AND 9"]
+    preds = [esc.Predicate(tbl, x, proj) for x in texts]
+    expect = [oracle.select(x, host, proj) for x in texts]
+    rows = [p.alloc_rows(len(e[0]) + 1) if j % 2 == 0 else None for j, (p, e) in enumerate(zip(preds, expect))]
+    counts, st = esc.esc_selectivity_batch([tbl.handle] * len(texts), [p.handle for p in preds], rows)
+    assert st == esc.ESC_OK and counts == [len(e[0]) for e in expect]
+    for r, (ids, pv) in zip(rows, expect):
+        if r is not None:
+            assert np.array_equal(r[1][:len(ids)].cpu().numpy().view(np.uint32), ids)
+            for name, c in zip(proj, r[2]):
+                assert np.array_equal(c[:len(ids)].cpu().numpy(), pv[name])
+    b = esc.esc_batch_prepare([tbl.handle] * len(texts), [p.handle for p in preds], rows)
+    dev_counts = torch.zeros(len(texts), dtype=torch.int64, device="cuda")
+    done = torch.zeros(len(texts), dtype=torch.int64, device="cuda")
+    esc.esc_batch_run(b, dev_counts, done)
+    torch.cuda.synchronize()
+    assert dev_counts.tolist() == counts and bool((done > 0).all())
+    esc.esc_batch_destroy(b)
+    dev_counts.zero_()
+    done.zero_()
+    esc.esc_selectivity_batch_async([tbl.handle] * len(texts), [p.handle for p in preds], dev_counts, rows, done)
+    torch.cuda.synchronize()
+    assert dev_counts.tolist() == counts and bool((done > 0).all())
+    # all constant: nothing to scan at all
+    consts = [preds[0], preds[2], preds[3]]
+    c2, _ = esc.esc_selectivity_batch([tbl.handle] * 3, [p.handle for p in consts])
+    assert c2 == [0, 0, t.nrows]
+
+
 def test_bitmap_and_semijoin(esc):
     dims_rows = datagen.STAR_DIM_ROWS
     fact = datagen.star_fact(3_000_017, seed=4, device="cuda", dim_rows=dims_rows)
