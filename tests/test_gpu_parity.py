@@ -145,6 +145,40 @@ def test_skewed_full_size(esc):
         _check(esc, host, tbl, text, datagen.SKEWED_PROJECTION)
 
 
+def test_skewed_full_size_every_predicate(esc):
+    """All 200 predicates of the benchmark at 60M rows, in select mode as it
+    runs them: properties that hold at any size (count = count-mode count,
+    ids strictly increasing and in range, projected values = the table's
+    values at those ids), and 64 sampled rows per predicate decided by the
+    oracle one by one (a 64-row table of those rows) against membership in
+    the returned ids."""
+    t = datagen.skewed_table(60_000_000, seed=2, device="cuda")
+    tbl = esc.Table.from_datagen(t)
+    proj = datagen.SKEWED_PROJECTION
+    rng = np.random.default_rng(11)
+    for j, pd in enumerate(datagen.skewed_predicates(200)):
+        p = esc.Predicate(tbl, pd.text, proj)
+        n_count = esc.count(tbl, p)
+        n, ids, cols = esc.select(tbl, p, capacity=n_count)
+        assert n == n_count == ids.numel(), j
+        ids64 = ids.to(torch.int64) & 0xffffffff
+        if n:
+            assert int(ids64[0]) >= 0 and int(ids64[-1]) < t.nrows
+            assert bool((ids64[1:] > ids64[:-1]).all()), j
+            for name, c in zip(proj, cols):
+                assert torch.equal(c, t.col(name).data.index_select(0, ids64)), (j, name)
+        sample = np.sort(rng.choice(t.nrows, 64, replace=False))
+        sidx = torch.from_numpy(sample).cuda()
+        host = {c.name: c.data.index_select(0, sidx).cpu().numpy() for c in t.columns}
+        for c in t.columns:
+            if c.dtype == "u16":
+                host[c.name] = host[c.name].view(np.uint16)
+        want = np.zeros(64, dtype=bool)
+        want[oracle.select(pd.text, host)[0].astype(np.int64)] = True
+        got = torch.isin(sidx, ids64).cpu().numpy()
+        assert np.array_equal(got, want), (j, pd.text)
+
+
 def test_async_and_two_streams(esc):
     t = datagen.single_table(3_000_000, seed=8, device="cuda")
     host = t.host()
