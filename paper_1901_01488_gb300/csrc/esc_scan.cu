@@ -1034,6 +1034,14 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     }
   }
   const uint32_t u = blockIdx.x - Q->wunit_base;
+  if (__ldcg(&Q->unit_total[u]) == 0) {
+    // no qualifying row in this unit: nothing to write, nothing to publish
+    if (Q->done_ns && threadIdx.x == 0) {
+      __threadfence();
+      if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
+    }
+    return;
+  }
   const uint32_t urows = Q->unit_tiles * Q->tile_rows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
