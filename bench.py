@@ -537,7 +537,7 @@ def run_serve(args):
         done = srv.run(reqs)
         s = serve.latency_summary(done)
         rows = sum(sizes[r.table] for r in done)
-        s.update({"rate_per_s": rate, "waves": srv.waves,
+        s.update({"rate_per_s": rate, "waves": srv.waves, "shared_scans": srv.shared_launches,
                   "offered_rows_per_s": rows / (nreq / rate)})
         results[f"rate_{int(rate)}"] = s
     out = {"metric": METRIC, "workload": "serve", "unit": "sub-queries/s",

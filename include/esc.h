@@ -215,6 +215,18 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
                                        int32_t n, const esc_rows *rows, uint64_t *dev_counts,
                                        uint64_t *dev_done_ns, void *stream);
 
+/* Count-only sub-queries of many predicates on one table in one pass over
+ * it (a shared scan; not in the paper): every tile of the union of the
+ * columns the predicates read is staged once and each predicate evaluated on
+ * it.  preds: n (>= 1) predicates compiled against `table` (projections are
+ * ignored); dev_counts: device array receiving the n exact counts, in the
+ * order of preds, when the stream reaches that point.  Predicates are taken
+ * in passes whose read columns fit the 16 stage slots, at most 2048 per
+ * pass.  Does not synchronise; host arrays may be freed on return.
+ * ESC_EINVAL for a NULL argument or a predicate of another table. */
+esc_status esc_selectivity_shared_async(const esc_table *table, const esc_pred *const *preds, int32_t n,
+                                        uint64_t *dev_counts, void *stream);
+
 /* One-shot form of the above: prepares, runs, synchronises and destroys.
  * counts is a host array of n entries. */
 esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred *const *preds,

@@ -1188,6 +1188,183 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   }
 }
 
+// ------------------------------------------------------------------ the shared scan
+// Count-only sub-queries of several predicates on one table with one pass
+// over it: each tile of the union of the columns they read is staged once
+// (the scan kernel's producer), and every predicate is evaluated on it.
+// L.q0 is the union layout (columns, tile and unit sizes; no program);
+// L.queries holds the nq predicates, compiled against that layout (their
+// stage offsets point into the union stage).  Consumers claim (predicate,
+// pair of groups) items of a stage predicate-major -- consecutive items of a
+// warp share a program, which stays in L1 -- and add each predicate's count
+// into shared counters, flushed once per CTA into L.queries[k].count.
+constexpr int kSharedMaxQueries = 2048;
+
+struct SharedSmem {
+  static constexpr size_t stages = 0;
+  static constexpr size_t bars = stages + (size_t)kStages * kStageBytes;
+  static constexpr size_t meta = bars + 2 * kStages * 8;
+  static constexpr size_t take = meta + kStages * sizeof(StageMeta);
+  static constexpr size_t cnt = (take + kStages * 4 + 15) & ~(size_t)15;
+  static constexpr size_t total = cnt + kSharedMaxQueries * 4;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) shared_kernel(const __grid_constant__ Launch L) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *stages = smem + SharedSmem::stages;
+  uint64_t *full_bar = reinterpret_cast<uint64_t *>(smem + SharedSmem::bars);
+  uint64_t *empty_bar = full_bar + kStages;
+  StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SharedSmem::meta);
+  uint32_t *take = reinterpret_cast<uint32_t *>(smem + SharedSmem::take);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + SharedSmem::cnt);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  ScratchHdr *hdr = L.hdr;
+  const Query &Y = L.q0;  // the union layout
+  const int nq = L.nq;
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) cnt[k] = 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full_bar[st], 1);
+      mbar_init(&empty_bar[st], kConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    int s = 0;
+    uint32_t phase = 0;
+    bool done = false;
+    uint32_t u_next = 0, dead_next = 0;
+    if (lane == 0) u_next = atomicAdd(&hdr->ticket, 1u);
+    while (!done) {
+      uint32_t u = 0, dead = 0;
+      if (lane == 0) {
+        u = u_next;
+        dead = dead_next;
+        if (u < L.total_units && !dead) {
+          u_next = atomicAdd(&hdr->ticket, 1u);
+          dead_next = aborted(hdr) ? 1u : 0u;
+        }
+      }
+      u = __shfl_sync(FULL, u, 0);
+      dead = __shfl_sync(FULL, dead, 0);
+      if (u >= L.total_units || dead) {
+        if (mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true) && lane == 0) {
+          meta[s].q = -1;
+          mbar_arrive(&full_bar[s]);
+        }
+        break;
+      }
+      const uint32_t t0 = u * Y.unit_tiles;
+      const uint32_t t1 = min(t0 + Y.unit_tiles, Y.ntiles);
+      for (uint32_t tile = t0; tile < t1; ++tile) {
+        if (!mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true)) {
+          done = true;
+          break;
+        }
+        const uint32_t r0 = tile * Y.tile_rows;
+        const uint32_t rows = min(Y.tile_rows, Y.nrows - r0);
+        uint8_t *stage = stages + (size_t)s * kStageBytes;
+        uint32_t bulk = 0, tail = 0;
+        const uint8_t *src = nullptr;
+        uint8_t *dst = nullptr;
+        const int nref = Y.nref;
+        if (lane < nref) {
+          const uint32_t w = Y.ref_w[lane];
+          const uint32_t bytes = rows * w;
+          bulk = bytes & ~15u;
+          tail = bytes - bulk;
+          src = Y.ref_ptr[lane] + (size_t)r0 * w;
+          dst = stage + Y.stage_off[lane];
+        }
+        if (__ballot_sync(FULL, tail != 0)) {
+          for (int c = 0; c < nref; ++c) {
+            const uint32_t tb = __shfl_sync(FULL, tail, c);
+            const uint32_t bb = __shfl_sync(FULL, bulk, c);
+            const uint8_t *sp = reinterpret_cast<const uint8_t *>(__shfl_sync(FULL, (unsigned long long)src, c));
+            uint8_t *dp = reinterpret_cast<uint8_t *>(__shfl_sync(FULL, (unsigned long long)dst, c));
+            if ((uint32_t)lane < tb) dp[bb + lane] = sp[bb + lane];
+          }
+          fence_proxy_async_smem();
+        }
+        const uint32_t tot = __reduce_add_sync(FULL, bulk);
+        __syncwarp();
+        if (lane == 0) {
+          StageMeta &m = meta[s];
+          take[s] = 0;
+          m.q = 0;
+          m.tile = tile;
+          m.rows = rows;
+          m.dead = dead;
+          m.unit = u;
+          mbar_arrive_expect_tx(&full_bar[s], tot);
+        }
+        __syncwarp();
+        if (bulk) bulk_load(dst, src, bulk, &full_bar[s]);
+        if (++s == kStages) {
+          s = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumers
+  int s = 0;
+  uint32_t phase = 0;
+  int acc_q = -1;
+  uint32_t acc = 0;
+  while (true) {
+    const bool got = mbar_wait(&full_bar[s], phase, hdr);
+    const StageMeta mt = meta[s];
+    if (!got || mt.q < 0) break;
+    if (mt.dead == 0) {
+      const uint8_t *stage = stages + (size_t)s * kStageBytes;
+      const uint32_t rows = mt.rows;
+      const int ngroups = (int)((rows + kGroup - 1) / kGroup);
+      const int npairs = (ngroups + 1) >> 1;
+      const int items = npairs * nq;
+      for (;;) {
+        int j = 0;
+        if (lane == 0) j = (int)atomicAdd(&take[s], 1u);
+        j = __shfl_sync(FULL, j, 0);
+        if (j >= items) break;
+        const int qi = j / npairs;
+        const int g = 2 * (j - qi * npairs), g1 = g + 1;
+        if (qi != acc_q) {
+          const uint32_t t = __reduce_add_sync(FULL, acc);
+          if (lane == 0 && t) atomicAdd(&cnt[acc_q], t);
+          acc = 0;
+          acc_q = qi;
+        }
+        const int gs[2] = {g, g1 < ngroups ? g1 : g};
+        uint32_t mm[2];
+        eval_groups<2>(&L.queries[qi], stage, gs, lane, mm);
+        acc += __popc(mm[0] & valid_mask(g, lane, rows));
+        if (g1 < ngroups) acc += __popc(mm[1] & valid_mask(g1, lane, rows));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[s]);
+    if (++s == kStages) {
+      s = 0;
+      phase ^= 1u;
+    }
+  }
+  if (acc_q >= 0) {
+    const uint32_t t = __reduce_add_sync(FULL, acc);
+    if (lane == 0 && t) atomicAdd(&cnt[acc_q], t);
+  }
+  // the consumer warps only (the producer has returned): then flush
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumers * 32) : "memory");
+  for (int k = (int)threadIdx.x - 32; k < nq; k += kConsumers * 32)
+    if (cnt[k]) atomicAdd(L.queries[k].count, (unsigned long long)cnt[k]);
+}
+
 // A program that reads no column is a constant (the compiler folded it:
 // e.g. a conjunction of contradictory tests): its result needs no scan.
 // Writes the count, and for a constant TRUE the caller's bitmap words or the
@@ -1277,6 +1454,7 @@ esc_status device_state(DeviceState **out) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
     ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
+    ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
     ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
     cudaMemPoolProps props;
@@ -1886,6 +2064,92 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   return s;
 }
 
+// One shared scan: `n` count-only predicates of table t whose read columns
+// (union `ucols`, table column indices) fit one stage layout.
+static esc_status run_shared_group(const esc_table *t, const esc_pred *const *preds, int32_t n,
+                                   const std::vector<int32_t> &ucols, uint64_t *dev_counts, cudaStream_t st) {
+  DeviceState *d;
+  esc_status s = device_state(&d);
+  if (s != ESC_OK) return s;
+  Launch L;
+  std::memset(&L, 0, sizeof L);
+  Query &Y = L.q0;
+  Y.nrows = (uint32_t)t->nrows;
+  Y.mode = MODE_COUNT;
+  Y.nref = (int32_t)ucols.size();
+  for (size_t k = 0; k < ucols.size(); ++k) {
+    Y.ref_w[k] = (uint8_t)dtype_width(t->dtypes[ucols[k]]);
+    Y.ref_ptr[k] = static_cast<const uint8_t *>(t->data[ucols[k]]);
+  }
+  layout_stage(Y, d->sms, kDefaultTuning);
+  std::vector<Query> qs((size_t)n);
+  for (int k = 0; k < n; ++k) {
+    if ((s = prepare_query(t, preds[k], nullptr, MODE_COUNT, &qs[k])) != ESC_OK) return s;
+    auto uslot = [&](int local) {
+      const int32_t col = preds[k]->ref_cols[local];
+      return (int)(std::find(ucols.begin(), ucols.end(), col) - ucols.begin());
+    };
+    for (int pc = 0; pc < qs[k].ninstr; ++pc) {  // stage offsets into the union layout
+      Instr &I = qs[k].code[pc];
+      if (I.op == OP_RANGE || I.op == OP_IN || I.op == OP_INSET || I.op == OP_UDF)
+        I.soff = (uint16_t)Y.stage_off[uslot(I.ref)];
+      if (I.op == OP_UDF) I.soff2 = (uint16_t)Y.stage_off[uslot(I.ref2)];
+    }
+  }
+  const size_t head = 256;
+  const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
+  const size_t q_bytes = sizeof(Query) * (size_t)n;
+  void *mem = nullptr;
+  if ((s = alloc_async(&mem, head + cnt_bytes + q_bytes, st)) != ESC_OK) return s;
+  uint8_t *base = static_cast<uint8_t *>(mem);
+  unsigned long long *counts = reinterpret_cast<unsigned long long *>(base + head);
+  Query *dq = reinterpret_cast<Query *>(base + head + cnt_bytes);
+  for (int k = 0; k < n; ++k) qs[k].count = &counts[k];
+  cudaError_t e = cudaMemsetAsync(base, 0, head + cnt_bytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dq, qs.data(), q_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && Y.nunits > 0) {
+    L.queries = dq;
+    L.nq = n;
+    L.total_units = Y.nunits;
+    L.hdr = reinterpret_cast<ScratchHdr *>(base);
+    const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), Y.nunits);
+    shared_kernel<<<grid, kThreads, SharedSmem::total, st>>>(L);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
+  cudaFreeAsync(mem, st);
+  if (e != cudaSuccess) return fail(ESC_ECUDA, std::string("esc_selectivity_shared_async: ") + cudaGetErrorString(e));
+  return ESC_OK;
+}
+
+esc_status esc_selectivity_shared_async(const esc_table *t, const esc_pred *const *preds, int32_t n,
+                                        uint64_t *dev_counts, void *stream) {
+  if (!t || !preds || n < 1 || !dev_counts)
+    return fail(ESC_EINVAL, "esc_selectivity_shared_async: need a table, n >= 1 predicates and dev_counts");
+  for (int i = 0; i < n; ++i)
+    if (!preds[i] || preds[i]->table != t)
+      return fail(ESC_EINVAL, "esc_selectivity_shared_async: every predicate must be compiled against the table");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // greedy groups: the union of read columns fits the stage layout
+  int i = 0;
+  while (i < n) {
+    std::vector<int32_t> ucols;
+    int j = i;
+    for (; j < n && j - i < kSharedMaxQueries; ++j) {
+      std::vector<int32_t> add;
+      for (int32_t c : preds[j]->ref_cols)
+        if (std::find(ucols.begin(), ucols.end(), c) == ucols.end()) add.push_back(c);
+      if (ucols.size() + add.size() > (size_t)kMaxRef) break;
+      ucols.insert(ucols.end(), add.begin(), add.end());
+    }
+    esc_status s = run_shared_group(t, preds + i, j - i, ucols, dev_counts + i, st);
+    if (s != ESC_OK) return s;
+    i = j;
+  }
+  clear_error();
+  return ESC_OK;
+}
+
 esc_status esc_timestamp(uint64_t *dev_ns, void *stream) {
   if (!dev_ns) return fail(ESC_EINVAL, "esc_timestamp: dev_ns is NULL");
   timestamp_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<unsigned long long *>(dev_ns));
@@ -1957,6 +2221,7 @@ esc_status noalloc_device(NoAllocDevice **out) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
     ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
+    ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
     ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
     void *p = nullptr;

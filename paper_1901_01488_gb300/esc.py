@@ -73,6 +73,7 @@ _sig = {
                        ctypes.POINTER(ctypes.c_int32)], _S),
     "esc_selftest_wait_timeout": ([ctypes.c_uint64, _P], _S),
     "esc_timestamp": ([_P, _P], _S),
+    "esc_selectivity_shared_async": ([_P, ctypes.POINTER(_P), ctypes.c_int32, _P, _P], _S),
     "esc_selectivity_batch_async": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32,
                                      ctypes.POINTER(esc_rows), _P, _P, _P], _S),
     "esc_mlp_forward": ([_P, ctypes.c_uint64, _P, _P, _P, _P], _S),
@@ -266,6 +267,14 @@ def esc_selectivity_batch_async(tables: Sequence[int], preds: Sequence[int], dev
         arr, keep = _rows_array(rows)
         _check(_lib.esc_selectivity_batch_async(ta, pa, n, arr, dev_counts.data_ptr(), done, _stream(stream)),
                "esc_selectivity_batch_async")
+
+
+def esc_selectivity_shared_async(table: int, preds: Sequence[int], dev_counts: torch.Tensor, stream=None) -> None:
+    """Counts of many predicates of one table in one pass over it (shared scan)."""
+    n = len(preds)
+    pa = (_P * n)(*preds)
+    _check(_lib.esc_selectivity_shared_async(table, pa, n, dev_counts.data_ptr(), _stream(stream)),
+           "esc_selectivity_shared_async")
 
 
 def esc_bitmap_build(dim: int, pred: int, dev_bitmap: torch.Tensor, stream=None) -> int:

@@ -6,7 +6,10 @@ a selection, Sec. 2); this is the serving pattern around it.  Requests
 flight: whenever a stream is free it admits every request that has arrived,
 up to `max_batch` and within the device-memory budget (each request reserves
 the scratch and output bytes its materialisation needs), compiles their
-predicates and launches them as one batch (esc_selectivity_batch_async).
+predicates and launches them: count requests on one table, when at least
+`shared_min` of them arrived together, share one pass over it
+(esc_selectivity_shared_async); the others run as one batch
+(esc_selectivity_batch_async).
 Waves on different streams overlap on the GPU.  A request's latency runs
 from its arrival to the host observing its wave's completion event.
 """
@@ -46,7 +49,7 @@ def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
 
 class Server:
     def __init__(self, esc, tables, mem_budget: int = 8 << 30, max_batch: int = 512, streams: int = 2,
-                 device="cuda"):
+                 device="cuda", shared_min: int = 8):
         self.esc = esc
         self.tables = tables
         self.budget = mem_budget
@@ -57,6 +60,8 @@ class Server:
         self.in_flight_bytes = 0
         self.peak_bytes = 0
         self.waves = 0
+        self.shared_min = shared_min      # count requests per table that share one pass
+        self.shared_launches = 0
 
     def run(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Request]:
         """Serves `requests` (arrival times relative to the start) and returns them completed."""
@@ -104,6 +109,15 @@ class Server:
 
     def _launch(self, batch: List[Request], k: int, st, nbytes: int, slots) -> None:
         esc = self.esc
+        # count requests on one table, when there are enough of them, share one
+        # pass over it; the rest run as one batch.  Shared groups come first.
+        per_table: Dict[int, List[Request]] = {}
+        for r in batch:
+            if not r.proj:
+                per_table.setdefault(r.table, []).append(r)
+        shared = {ti for ti, rs in per_table.items() if len(rs) >= self.shared_min}
+        batch = ([r for r in batch if not r.proj and r.table in shared] +
+                 [r for r in batch if r.proj or r.table not in shared])
         preds = []
         rows = []
         for r in batch:
@@ -117,8 +131,20 @@ class Server:
                 rows.append(None)
         counts = torch.zeros(len(batch), dtype=torch.int64, device=self.device)
         with torch.cuda.stream(st):
-            esc.esc_selectivity_batch_async([self.tables[r.table].handle for r in batch], [p.handle for p in preds],
-                                            counts, rows if any(x is not None for x in rows) else None, None, st)
+            i = 0
+            while i < len(batch) and not batch[i].proj and batch[i].table in shared:
+                j = i
+                while j < len(batch) and not batch[j].proj and batch[j].table == batch[i].table:
+                    j += 1
+                esc.esc_selectivity_shared_async(self.tables[batch[i].table].handle, [p.handle for p in preds[i:j]],
+                                                 counts[i:j], st)
+                self.shared_launches += 1
+                i = j
+            if i < len(batch):
+                rest = rows[i:]
+                esc.esc_selectivity_batch_async([self.tables[r.table].handle for r in batch[i:]],
+                                                [p.handle for p in preds[i:]], counts[i:],
+                                                rest if any(x is not None for x in rest) else None, None, st)
             ev = torch.cuda.Event()
             ev.record(st)
         self.in_flight_bytes += nbytes

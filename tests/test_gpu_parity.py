@@ -268,6 +268,48 @@ def test_batch_with_constant_programs(esc):
     assert c2 == [0, 0, t.nrows]
 
 
+def test_shared_scan(esc):
+    """Counts of many predicates in one pass (shared scan) equal the oracle's:
+    random predicates over every type on a ragged table, passes split by the
+    16 stage slots (a 20-column table), more than 2048 predicates, an empty
+    table."""
+    n = 100_003
+    cols = host_table(n, seed=13)
+    t = esc.Table(as_columns(cols, "cuda"), n)
+    texts, preds = [], []
+    for x in random_preds(300, seed=23):
+        try:
+            preds.append(esc.Predicate(t, x))
+            texts.append(x)
+        except esc.EscError:
+            pass
+    dev = torch.zeros(len(preds), dtype=torch.int64, device="cuda")
+    esc.esc_selectivity_shared_async(t.handle, [p.handle for p in preds], dev)
+    assert dev.tolist() == [oracle.count(x, cols) for x in texts]
+    # 20 columns: one predicate per column pair, so the union exceeds 16 slots
+    rng = np.random.default_rng(3)
+    wide = {f"x{k}": rng.integers(-1000, 1000, 50_001).astype(np.int32) for k in range(20)}
+    tw = esc.Table(as_columns(wide, "cuda"), 50_001)
+    wtexts = [f"x{k} > {int(rng.integers(-900, 900))} AND x{(k + 7) % 20} < {int(rng.integers(-900, 900))}"
+              for k in range(20)] * 3
+    wp = [esc.Predicate(tw, x) for x in wtexts]
+    dev = torch.zeros(len(wp), dtype=torch.int64, device="cuda")
+    esc.esc_selectivity_shared_async(tw.handle, [p.handle for p in wp], dev)
+    assert dev.tolist() == [oracle.count(x, wide) for x in wtexts]
+    # more than one pass of 2048 predicates
+    many = [preds[k % len(preds)] for k in range(2100)]
+    dev = torch.zeros(len(many), dtype=torch.int64, device="cuda")
+    esc.esc_selectivity_shared_async(t.handle, [p.handle for p in many], dev)
+    single = [esc.count(t, p) for p in preds]
+    assert dev.tolist() == [single[k % len(preds)] for k in range(2100)]
+    # an empty table
+    t0 = esc.Table(as_columns({k: v[:0] for k, v in cols.items()}, "cuda"), 0)
+    p0 = [esc.Predicate(t0, "a > 1"), esc.Predicate(t0, "TRUE")]
+    dev = torch.full((2,), 7, dtype=torch.int64, device="cuda")
+    esc.esc_selectivity_shared_async(t0.handle, [p.handle for p in p0], dev)
+    assert dev.tolist() == [0, 0]
+
+
 def test_bitmap_and_semijoin(esc):
     dims_rows = datagen.STAR_DIM_ROWS
     fact = datagen.star_fact(3_000_017, seed=4, device="cuda", dim_rows=dims_rows)

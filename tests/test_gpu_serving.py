@@ -38,6 +38,7 @@ def test_served_results_equal_alone(esc):
     srv = serve.Server(esc, etabs, mem_budget=256 << 20, max_batch=64, streams=2)
     done = srv.run(reqs)
     assert srv.waves > 1
+    assert srv.shared_launches > 0          # same-table count requests shared a pass
     assert srv.peak_bytes <= 256 << 20 or max(serve.request_bytes(etabs[r.table].nrows, r, srv.widths[r.table])
                                                for r in reqs) > 256 << 20
     for r in done:
