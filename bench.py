@@ -614,7 +614,7 @@ def run_surrogate(args):
     t0 = time.perf_counter()
     counts = S.exact_counts(esc, table, preds)
     label_s = time.perf_counter() - t0
-    # device time of the labelling launches alone, on a 65,536-pair slice with predicates compiled beforehand
+    # device time of the labelling passes alone, on a 65,536-pair slice with predicates compiled beforehand
     sl = preds[:65_536]
     comp = [esc.Predicate(table, p.text) for p in sl]
     dc = torch.zeros(len(comp), dtype=torch.int64, device=dev)
@@ -623,7 +623,7 @@ def run_surrogate(args):
     a.record(st)
     for s0 in range(0, len(comp), 2048):
         ch = comp[s0:s0 + 2048]
-        esc.esc_selectivity_batch_async([table.handle] * len(ch), [p.handle for p in ch], dc[s0:s0 + len(ch)])
+        esc.esc_selectivity_shared_async(table.handle, [p.handle for p in ch], dc[s0:s0 + len(ch)])
     b.record(st)
     torch.cuda.synchronize()
     dev_ms = a.elapsed_time(b)
@@ -659,7 +659,7 @@ def run_surrogate(args):
                                   f"accumulate; 90/10 split", "data": "synthetic"},
            "labels": {"wall_s": label_s, "per_s": n / label_s, "predicate_generation_s": gen_s,
                       "device_ms_per_65536": dev_ms, "device_labels_per_s": len(comp) / (dev_ms / 1e3),
-                      "same_counts_async_and_batched": True},
+                      "labels_by": "shared scans of 2048 predicates"},
            "training": {"epochs": epochs, "samples": ntr, "wall_s": train_s, "loss_first_last": [curve[0], curve[-1]],
                         "samples_per_s": ntr * epochs / train_s},
            "inference": {"samples": n - ntr, "ms": pred_ms, "samples_per_s": (n - ntr) / (pred_ms / 1e3),
