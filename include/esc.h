@@ -259,8 +259,8 @@ esc_status esc_semijoin_counts(const esc_table *fact, const char *const *fk_cols
 /* ---------------------------------------------------------------- learned surrogate */
 
 /* A learned selectivity estimator built on top of ESC (not in the paper; the
- * paper's counts are exact -- this network is trained on them and judged by
- * them): an MLP 64 -> 128 -> ReLU -> 128 -> ReLU -> 1 mapping encoded
+ * paper's counts are exact -- this network is trained on them and evaluated
+ * against them): an MLP 64 -> 128 -> ReLU -> 128 -> ReLU -> 1 mapping encoded
  * predicate features to log10 selectivity.  Parameters are one flat array
  * of ESC_MLP_PARAMS floats: W1 [128][64] row-major, b1 [128], W2 [128][128],
  * b2 [128], w3 [128], b3.  `w_bf16` is a bfloat16 copy of the same array

@@ -1,7 +1,7 @@
 """FP64 forward / backward of the selectivity-surrogate MLP -- TEST INFRASTRUCTURE.
 
 The surrogate is not in the paper (it is this project's learned estimator,
-judged by exact selectivity computation).  Network: x (64) -> W1 x + b1 ->
+evaluated against exact selectivity computation).  Network: x (64) -> W1 x + b1 ->
 ReLU -> W2 h1 + b2 -> ReLU -> w3 . h2 + b3 = y (the predicted log10
 selectivity); loss = mean over the batch of (y - t)^2.
 

@@ -1,4 +1,4 @@
-// Learned selectivity surrogate (not in the paper; judged by exact ESC):
+// Learned selectivity surrogate (not in the paper; evaluated against exact ESC):
 // an MLP 64 -> 128 -> ReLU -> 128 -> ReLU -> 1 predicting log10 selectivity
 // from encoded predicate features.  Weights are used in bfloat16, biases
 // and every accumulation are float32, the optimiser keeps float32 master

@@ -1,9 +1,9 @@
-"""Learned selectivity surrogate, trained on and judged by exact ESC.
+"""Learned selectivity surrogate, trained on and evaluated against exact ESC.
 
 Not in the paper: the paper computes every selectivity exactly (Sec. 2).
 This module adds a small network that *estimates* log10 selectivity from
 the predicate alone, trained on (predicate, exact count) pairs that ESC
-itself produces; exact ESC stays the judge (q-error) and the fallback, and
+itself produces; exact ESC stays the reference (q-error) and the fallback, and
 is the only source of counts a planner may treat as exact.
 
 * encode(): 64 features = 8 column slots x [present, lo, hi, is_eq, is_in,

@@ -1,5 +1,5 @@
 """The learned surrogate's kernels against the FP64 oracle, and its training
-and accuracy with exact ESC as the judge."""
+and accuracy evaluated against exact ESC."""
 import time
 
 import numpy as np
