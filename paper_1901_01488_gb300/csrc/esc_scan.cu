@@ -16,7 +16,7 @@
 //    and interpret the postfix program on 8 rows per lane, keeping the
 //    boolean evaluation stack as 8-bit masks in one 64-bit register;
 //  * counts: popc per lane, one atomic per warp and query;
-//  * ordered compaction, first pass: the selection bitmap (lane order),
+//  * ordered compaction, first pass: the selection bitmap (lane-major),
 //    staged per tile in shared memory and written with one bulk copy, and a
 //    total per work unit; second pass (write_kernel, one block per unit): a
 //    decoupled look-back over the unit totals (Merrill & Garland,
@@ -741,25 +741,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
           uint32_t word = 0;
           if (mode == MODE_SELECT) {
             uacc += c;
-            // selection bitmap in lane order: word p = the lanes' mask bit p,
-            // i.e. bit l of word p is row 64*(p/2) + 2*l + p%2 of the group
-            // (the write kernel counts a group's rows from its words)
-            uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-            if (__any_sync(FULL, m != 0u)) {
-              lo.x = __ballot_sync(FULL, m & 1u);
-              lo.y = __ballot_sync(FULL, m & 2u);
-              lo.z = __ballot_sync(FULL, m & 4u);
-              lo.w = __ballot_sync(FULL, m & 8u);
-              hi.x = __ballot_sync(FULL, m & 16u);
-              hi.y = __ballot_sync(FULL, m & 32u);
-              hi.z = __ballot_sync(FULL, m & 64u);
-              hi.w = __ballot_sync(FULL, m & 128u);
-            }
-            if (lane == 0) {
-              uint4 *dst = reinterpret_cast<uint4 *>(rbm + gs[i] * 8);
-              dst[0] = lo;
-              dst[1] = hi;
-            }
+            // selection bitmap, lane-major: byte l of the group's 32 bytes is
+            // lane l's mask (bit 2j+i: row 64*j + 2*l + i of the group); the
+            // write kernel counts a group's rows from its bytes
+            reinterpret_cast<uint8_t *>(rbm)[gs[i] * 32 + lane] = (uint8_t)m;
             continue;
           }
           const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
@@ -825,9 +810,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
 //     lane, which walks its group's rows in order and stages (row, slot)
 //     entries; the warp then copies the staged entries, 4 per lane, loads
 //     before stores.
-// The selection bitmap is in lane order (see the scan kernel): bit l of the
-// group's word p is its row 64*(p/2) + 2*l + p%2, so row order within a block
-// of 64 rows merges an even-row word and an odd-row word.
+// The selection bitmap is lane-major (see the scan kernel): bit 2j+i of the
+// group's byte l is its row 64*j + 2*l + i.
 
 constexpr int kWriteThreads = 256;
 constexpr int kWriteWarps = kWriteThreads / 32;
@@ -936,12 +920,6 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
   }
 }
 
-// Bits 0..3 of x to bits 0, 2, 4, 6.
-__device__ __forceinline__ uint32_t spread4(uint32_t x) {
-  x = (x | (x << 2)) & 0x33u;
-  return (x | (x << 1)) & 0x55u;
-}
-
 // One dense group, the whole warp.  The projected columns of all 256 rows
 // arrive together (16-byte asynchronous copies, at most kRawBytes at a
 // time; a column wider than that is read in place); each output slot then
@@ -949,10 +927,11 @@ __device__ __forceinline__ uint32_t spread4(uint32_t x) {
 __device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &W, int j, uint32_t g, uint32_t cnt,
                                             unsigned long long base, int lane) {
   const uint64_t cap = G.capacity;
-  // rows 8l .. 8l+7 of the group: bits 4(l%8) .. 4(l%8)+3 of the even-row
-  // and odd-row words of block l/8 (lane-order bitmap), interleaved
-  const uint32_t jj = (uint32_t)lane >> 3, sub = 4u * ((uint32_t)lane & 7u);
-  const uint32_t bits8 = spread4((W.words[j][2 * jj] >> sub) & 0xfu) | (spread4((W.words[j][2 * jj + 1] >> sub) & 0xfu) << 1);
+  // rows 8l .. 8l+7 of the group: bits 2(l/8), 2(l/8)+1 of bytes 4(l%8) ..
+  // 4(l%8)+3 (word l%8 of the lane-major bitmap), packed in row order
+  uint32_t x = (W.words[j][lane & 7] >> (2u * ((uint32_t)lane >> 3))) & 0x03030303u;
+  x = (x | (x >> 6)) & 0x000f000fu;
+  const uint32_t bits8 = (x | (x >> 12)) & 0xffu;
   const uint32_t cl = __popc(bits8);
   uint32_t incl = cl;
 #pragma unroll
@@ -1150,25 +1129,20 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
           // the group's first sc set bits are its rows: never read past sc
           const uint32_t eend = min(wend, sx + sc);
           uint32_t e = sx;  // staged index of this lane's next entry
-          // rows in order: within block j (rows 64j .. 64j+63), merge the
-          // even-row word 2j and the odd-row word 2j+1 of the lane-order bitmap
+          // rows in order: block j (rows 64j .. 64j+63) is bits 2j, 2j+1 of the
+          // 32 bytes (byte l: rows 64j + 2l + {0, 1}); words in order, bits
+          // ascending within a word, is row order
+#pragma unroll 1
+          for (uint32_t jb = 0; jb < 4; ++jb) {
 #pragma unroll
-          for (int jb = 0; jb < 4; ++jb) {
-            const uint4 &h = jb < 2 ? wlo : whi;
-            uint32_t ev = (jb & 1) ? h.z : h.x, od = (jb & 1) ? h.w : h.y;
-            while ((ev | od) != 0u && e < eend) {
-              const uint32_t pe = ev ? (uint32_t)__ffs(ev) - 1u : 32u;
-              const uint32_t po = od ? (uint32_t)__ffs(od) - 1u : 32u;
-              uint32_t rr;
-              if (pe <= po) {
-                rr = 2u * pe;
-                ev &= ev - 1u;
-              } else {
-                rr = 2u * po + 1u;
-                od &= od - 1u;
+            for (uint32_t wi = 0; wi < 8; ++wi) {
+              const uint4 &h = wi < 4 ? wlo : whi;
+              const uint32_t wv = (wi & 3) == 0 ? h.x : (wi & 3) == 1 ? h.y : (wi & 3) == 2 ? h.z : h.w;
+              for (uint32_t xm = wv & (0x03030303u << (2 * jb)); xm != 0u && e < eend; xm &= xm - 1u, ++e) {
+                const uint32_t bpos = (uint32_t)__ffs(xm) - 1u;  // 8 * byte + 2j + i
+                const uint32_t rr = 64u * jb + 2u * (4u * wi + (bpos >> 3)) + ((bpos & 7u) - 2u * jb);
+                if (e >= win) ent[e - win] = ((rrel + rr) << 16) | (srel + e - sx);
               }
-              if (e >= win) ent[e - win] = ((rrel + 64u * jb + rr) << 16) | (srel + e - sx);
-              ++e;
             }
           }
         }
