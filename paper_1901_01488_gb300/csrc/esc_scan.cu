@@ -982,11 +982,34 @@ __device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &
   } while (c0 < np);
 }
 
+// Look-back words: flag in bits 63..62 (2 = inclusive prefix published),
+// the value below.
+constexpr unsigned long long kLookFinal = 2ull << 62, kLookValue = (1ull << 62) - 1;
+constexpr int kLookPerThread = 4;
+
+// One look-back window: this thread's units idx - kLookPerThread*t - k; a
+// unit before the first reads as a published prefix of 0.
+__device__ __forceinline__ void lookback_load(const unsigned long long *st, const unsigned long long *tot,
+                                              long long idx, unsigned long long (&w)[kLookPerThread],
+                                              unsigned long long (&t)[kLookPerThread]) {
+#pragma unroll
+  for (int k = 0; k < kLookPerThread; ++k) {
+    const long long j = idx - (long long)kLookPerThread * threadIdx.x - k;
+    w[k] = kLookFinal;
+    t[k] = 0;
+    if (j >= 0) {
+      w[k] = ld_relaxed(&st[j]);
+      t[k] = __ldcg(&tot[j]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(16) uint8_t wsmem[];
   __shared__ GatherInfo G;
   __shared__ uint32_t wsum[kWriteWarps];
-  __shared__ unsigned long long s_excl;
+  __shared__ unsigned long long lb_val[2][kWriteWarps];  // look-back rounds, by parity
+  __shared__ uint32_t lb_hit[2][kWriteWarps];
   __shared__ int s_q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1013,14 +1036,6 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     }
   }
   const uint32_t u = blockIdx.x - Q->wunit_base;
-  if (__ldcg(&Q->unit_total[u]) == 0) {
-    // no qualifying row in this unit: nothing to write, nothing to publish
-    if (Q->done_ns && threadIdx.x == 0) {
-      __threadfence();
-      if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
-    }
-    return;
-  }
   const uint32_t urows = Q->unit_tiles * Q->tile_rows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
@@ -1031,13 +1046,28 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   const int gi = warp * gpw + lane;
   const bool valid = lane < gpw && gi < ng;
   const uint32_t grp_l = g0 + (uint32_t)gi;
-  // the group's bitmap words (the scan wrote all 8 words of every group) and
-  // its count
+  // Everything the block reads of the scan's output is requested at once:
+  // the unit's total, the bitmap words of this thread's group (the scan
+  // wrote all 8 words of every group) and the first look-back window.
+  const unsigned long long *tot = Q->unit_total;
+  unsigned long long *st = Q->unit_status;
+  const unsigned long long utot = __ldcg(&tot[u]);
   uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
   if (valid) {
     const uint4 *bw = reinterpret_cast<const uint4 *>(Q->bitmap + (size_t)grp_l * 8);
     wlo = __ldcg(bw);
     whi = __ldcg(bw + 1);
+  }
+  long long idx = (long long)u - 1;  // closest predecessor not yet accounted
+  unsigned long long lw[kLookPerThread], lt[kLookPerThread];
+  lookback_load(st, tot, idx, lw, lt);
+  if (utot == 0) {
+    // no qualifying row in this unit: nothing to write, nothing to publish
+    if (Q->done_ns && threadIdx.x == 0) {
+      __threadfence();
+      if (atomicSub(Q->tiles_left, 1u) == 1u) *Q->done_ns = globaltimer();
+    }
+    return;
   }
   const uint32_t c = __popc(wlo.x) + __popc(wlo.y) + __popc(wlo.z) + __popc(wlo.w) + __popc(whi.x) +
                      __popc(whi.y) + __popc(whi.z) + __popc(whi.w);
@@ -1048,52 +1078,49 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     if (lane >= o) inc += y;
   }
   if (lane == 31) wsum[warp] = inc;
-  if (warp == 0) {
-    // 8 predecessor units per lane per round trip; every aggregate is final
-    const unsigned long long FP = 2ull << 62, VM = (1ull << 62) - 1;
-    unsigned long long *st = Q->unit_status;
-    const unsigned long long *tot = Q->unit_total;
-    unsigned long long excl = 0;
-    long long idx = (long long)u - 1;  // closest predecessor not yet accounted
-    while (idx >= 0) {
-      unsigned long long sum = 0, pval = 0;  // this lane: totals before its closest published prefix
-      int kp = 8;                            // index of that prefix among the lane's 8 units, 8 = none
+  // The unit's first slot: a decoupled look-back over the unit totals, all
+  // of them final (the scan wrote them), so it never waits.  Each round the
+  // whole block covers kLookPerThread * kWriteThreads predecessors (thread t:
+  // units idx - kLookPerThread*t - k, closest first) and stops at the
+  // closest one whose inclusive prefix another block has published.
+  unsigned long long excl = 0;
+  for (int r = 0;; ++r) {
+    if (r > 0) lookback_load(st, tot, idx, lw, lt);
+    unsigned long long sum = 0, pval = 0;  // totals before the thread's closest published prefix
+    int kp = kLookPerThread;               // that prefix among the thread's units (none: kLookPerThread)
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const long long j = idx - 8 * lane - k;
-        unsigned long long w = FP, t = 0;  // before the first unit: prefix 0
-        if (j >= 0) {
-          w = ld_relaxed(&st[j]);
-          t = tot[j];
-        }
-        if (kp == 8) {
-          if ((w >> 62) == 2) {
-            kp = k;
-            pval = w & VM;
-          } else {
-            sum += t;
-          }
+    for (int k = 0; k < kLookPerThread; ++k) {
+      if (kp == kLookPerThread) {
+        if ((lw[k] >> 62) == 2) {
+          kp = k;
+          pval = lw[k] & kLookValue;
+        } else {
+          sum += lt[k];
         }
       }
-      const uint32_t pm = __ballot_sync(FULL, kp < 8);
-      if (pm) {
-        const int first = __ffs(pm) - 1;
-        excl += warp_sum(lane < first ? sum : lane == first ? sum + pval : 0ull);
-        break;
-      }
-      excl += warp_sum(sum);
-      idx -= 256;
     }
+    const uint32_t pm = __ballot_sync(FULL, kp < kLookPerThread);
+    const int first = pm ? __ffs(pm) - 1 : 32;
+    const unsigned long long v = warp_sum(lane < first ? sum : lane == first ? sum + pval : 0ull);
     if (lane == 0) {
-      st_relaxed(&st[u], FP | (excl + tot[u]));
-      s_excl = excl;
+      lb_val[r & 1][warp] = v;
+      lb_hit[r & 1][warp] = pm != 0u;
     }
+    __syncthreads();  // also publishes wsum and G
+    bool found = false;
+#pragma unroll 1
+    for (int w = 0; w < kWriteWarps && !found; ++w) {
+      excl += lb_val[r & 1][w];
+      found = lb_hit[r & 1][w] != 0;
+    }
+    if (found) break;
+    idx -= (long long)kLookPerThread * kWriteThreads;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) st_relaxed(&st[u], kLookFinal | (excl + utot));
   uint32_t wbase = 0;
   for (int i = 0; i < warp; ++i) wbase += wsum[i];
   if (wsum[warp] != 0) {
-    const unsigned long long pos_ref = s_excl + wbase;      // first slot of the warp's groups
+    const unsigned long long pos_ref = excl + wbase;        // first slot of the warp's groups
     const unsigned long long base_l = pos_ref + inc - c;    // first slot of this lane's group
     const uint32_t grow_l = grp_l * kGroup;
     const bool dense_l = valid && c >= kDenseMin && grow_l + kGroup <= G.nrows;
