@@ -6,8 +6,9 @@
 //
 // Kernel shape (sm_103a):
 //  * scan_kernel, persistent: one CTA per SM, 1 producer warp + kConsumers
-//    consumer warps; work units (a few consecutive tiles) are claimed in
-//    order from a global ticket;
+//    consumer warps (kConsumersLean in the instance for programs without a
+//    udf, whose register demand is lower); work units (a few consecutive
+//    tiles) are claimed in order from a global ticket;
 //  * the producer stages every column the predicate reads into shared memory
 //    with 1-D bulk TMA copies (cp.async.bulk ... mbarrier::complete_tx) into a
 //    ring of kStages stages; the ragged tail of the last tile (< 16 bytes per
@@ -39,6 +40,11 @@ namespace esc {
 
 constexpr int kConsumers = 15;                   // consumer warps per CTA
 constexpr int kThreads = 32 * (kConsumers + 1);  // + the producer warp: 16 warps, 4 per SM sub-partition
+// Programs without a udf: the udf remainder sets the kernel's register
+// demand (128 per thread), so a second instance of the scan kernel without
+// it runs more consumer warps per SM.
+constexpr int kConsumersLean = 19;
+constexpr int kThreadsLean = 32 * (kConsumersLean + 1);
 constexpr int kStages = 3;
 constexpr uint32_t kStageBytes = 64 * 1024;
 constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256: one write-kernel thread per group
@@ -304,7 +310,7 @@ __device__ __forceinline__ void udf_rem_small8(const int64_t (&a)[8], const int6
 // Runs the program on this lane's 8 rows of NG groups of the staged tile at
 // once (one decode per instruction for all of them, NG independent chains).
 // Q (program included) lives in shared memory.
-template <int NG>
+template <int NG, bool UDF>
 __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage, const int (&grp)[NG], int lane,
                                             uint32_t (&out)[NG]) {
   uint64_t S[NG];  // evaluation stacks: entry k in bits [8k, 8k+8), top at bits 0..7
@@ -416,7 +422,7 @@ __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage
               for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)(v[i][k] == c) << k;
           }
         }
-      } else {  // OP_UDF
+      } else if constexpr (UDF) {  // OP_UDF (a program with one never runs on the lean instance)
         const int dt2 = (int)((h.x >> 16) & 0xffu);
         const int w2 = width_of(dt2);
         const uint8_t *col2 = stage + (h.w & 0xffffu);
@@ -546,7 +552,9 @@ struct SmemLayout {
 // Warp 0: producer (unit tickets, bulk copies).  Warps 1..: consumers
 // (evaluate; count; compaction: bitmap words and unit totals; bitmap mode:
 // the caller's bitmap words).
-__global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant__ Launch L) {
+// NC consumer warps; UDF: the instance can run programs with a udf.
+template <int NC, bool UDF>
+__global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *stages = smem + SmemLayout::stages;
   Query *qslot = reinterpret_cast<Query *>(smem + SmemLayout::qslot);
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], kConsumers);
+      mbar_init(&empty_bar[s], NC);
       slotq[s] = -1;
       resdone[s] = 0;
     }
@@ -730,7 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
         const int g = 2 * j, g1 = g + 1;
         const int gs[2] = {g, g1 < ngroups ? g1 : g};
         uint32_t mm[2];
-        eval_groups<2>(Q, stage, gs, lane, mm);
+        eval_groups<2, UDF>(Q, stage, gs, lane, mm);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           if (i == 1 && g1 >= ngroups) break;
@@ -768,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_kernel(const __grid_constant
       uint32_t last = 0;
       if (lane == 0) {
         __threadfence_block();
-        last = atomicAdd(&resdone[s], 1u) == (uint32_t)kConsumers - 1u ? 1u : 0u;
+        last = atomicAdd(&resdone[s], 1u) == (uint32_t)NC - 1u ? 1u : 0u;
         __threadfence_block();
       }
       if (__shfl_sync(FULL, last, 0)) {
@@ -1344,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads, 1) shared_kernel(const __grid_consta
         }
         const int gs[2] = {g, g1 < ngroups ? g1 : g};
         uint32_t mm[2];
-        eval_groups<2>(&L.queries[qi], stage, gs, lane, mm);
+        eval_groups<2, true>(&L.queries[qi], stage, gs, lane, mm);
         acc += __popc(mm[0] & valid_mask(g, lane, rows));
         if (g1 < ngroups) acc += __popc(mm[1] & valid_mask(g1, lane, rows));
       }
@@ -1453,11 +1461,19 @@ esc_status device_state(DeviceState **out) {
   DeviceState &d = g_dev[dev];
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumers, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumersLean, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes()));
     ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
     ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel<kConsumers, true>, kThreads,
+                                                         smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
+    int lean = 0;
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lean, scan_kernel<kConsumersLean, false>, kThreadsLean,
+                                                         smem_bytes()));
+    if (lean < d.blocks_per_sm) return fail(ESC_ECUDA, "scan kernel (no udf) does not fit on an SM");
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
@@ -1476,6 +1492,17 @@ esc_status device_state(DeviceState **out) {
 // 256-row group, at most kMaxTileRows.
 // The value of a program that reads no column (TRUE, FALSE and connectives
 // only); false when the program reads a column.
+// Whether the program has a udf test: it then needs the scan kernel's udf
+// instance; every other program runs on the lean one.
+bool program_has_udf(const Query &q) {
+  for (int i = 0; i < q.ninstr; ++i)
+    if (q.code[i].op == OP_UDF) return true;
+  return false;
+}
+
+// Consumer warps of the scan kernel instance a launch uses.
+int scan_consumers(bool udf) { return udf ? kConsumers : kConsumersLean; }
+
 bool program_constant(const Query &q, uint32_t *value) {
   if (q.nref != 0) return false;
   uint8_t stack[kMaxDepth + 1];
@@ -1591,14 +1618,18 @@ esc_status alloc_async(void **p, size_t bytes, cudaStream_t st) {
   return ESC_OK;
 }
 
-esc_status launch_scan(const Launch &L, cudaStream_t st) {
+// udf: some program of the launch has a udf test (the udf instance runs it).
+esc_status launch_scan(const Launch &L, bool udf, cudaStream_t st) {
   DeviceState *d;
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   if (L.total_units == 0) return ESC_OK;
   const uint32_t cap = (uint32_t)(d->sms * d->blocks_per_sm);
   const uint32_t grid = std::min<uint32_t>(cap, L.total_units);
-  scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
+  if (udf)
+    scan_kernel<kConsumers, true><<<grid, kThreads, smem_bytes(), st>>>(L);
+  else
+    scan_kernel<kConsumersLean, false><<<grid, kThreadsLean, smem_bytes(), st>>>(L);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
@@ -1696,7 +1727,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   if (program_constant(L.q0, &cval)) {
     s = launch_const(L, cval, st);
   } else {
-    s = launch_scan(L, st);
+    s = launch_scan(L, program_has_udf(L.q0), st);
     if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
   }
   if (s != ESC_OK) {
@@ -1865,6 +1896,8 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   b->tiles_init = reinterpret_cast<unsigned int *>(b->scratch + b->scratch_bytes);
   uint8_t *op = b->scratch + b->scratch_bytes + left_bytes;
   std::vector<unsigned int> init((size_t)n);
+  bool udf = false;
+  for (int i = 0; i < n; ++i) udf = udf || (!qs[i].is_const && program_has_udf(qs[i]));
   for (int i = 0; i < n; ++i) {
     qs[i].count = &b->counts[i];
     qs[i].done_ns = &b->done[i];
@@ -1877,7 +1910,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       op += select_other_bytes(qs[i]);
       init[i] = qs[i].nunits;                         // counted down by the write kernel
     } else {
-      init[i] = qs[i].ntiles * (unsigned)kConsumers;  // counted down by the scan kernel
+      init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);  // counted down by the scan kernel
     }
   }
   if ((uintptr_t)op > (uintptr_t)base + total) {
@@ -1912,7 +1945,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
     if (!cidx.empty()) ls = launch_const_batch(b->queries, dev_cidx, (uint32_t)cidx.size(), cs);
-    if (ls == ESC_OK) ls = launch_scan(L, cs);
+    if (ls == ESC_OK) ls = launch_scan(L, udf, cs);
     if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
@@ -2019,6 +2052,8 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   uint8_t *zp = z + 256 + 2 * cnt_bytes + left_bytes;
   uint8_t *op = z + zbytes;
   std::vector<unsigned int> init((size_t)n);
+  bool udf = false;
+  for (int i = 0; i < n; ++i) udf = udf || (!qs[i].is_const && program_has_udf(qs[i]));
   for (int i = 0; i < n; ++i) {
     qs[i].count = &counts[i];
     qs[i].done_ns = dev_done_ns ? &done[i] : nullptr;
@@ -2031,7 +2066,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       op += select_other_bytes(qs[i]);
       init[i] = qs[i].nunits;
     } else {
-      init[i] = qs[i].ntiles * (unsigned)kConsumers;
+      init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);
     }
   }
   uint32_t *dev_cidx = reinterpret_cast<uint32_t *>(base + sizeof(Query) * (size_t)n);
@@ -2052,7 +2087,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   L.total_units = (uint32_t)units;
   L.hdr = reinterpret_cast<ScratchHdr *>(z);
   s = cidx.empty() ? ESC_OK : launch_const_batch(L.queries, dev_cidx, (uint32_t)cidx.size(), st);
-  if (s == ESC_OK) s = launch_scan(L, st);
+  if (s == ESC_OK) s = launch_scan(L, udf, st);
   if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, st);
   if (s == ESC_OK) {
     e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
@@ -2220,11 +2255,19 @@ esc_status noalloc_device(NoAllocDevice **out) {
   NoAllocDevice &d = g_noalloc[dev];
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumers, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes()));
+    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumersLean, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes()));
     ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
     ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel, kThreads, smem_bytes()));
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel<kConsumers, true>, kThreads,
+                                                         smem_bytes()));
     if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
+    int lean = 0;
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lean, scan_kernel<kConsumersLean, false>, kThreadsLean,
+                                                         smem_bytes()));
+    if (lean < d.blocks_per_sm) return fail(ESC_ECUDA, "scan kernel (no udf) does not fit on an SM");
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
@@ -2288,7 +2331,10 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
     if (cs != ESC_OK) return cs;
   } else if (L.total_units > 0) {
     const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), L.total_units);
-    scan_kernel<<<grid, kThreads, smem_bytes(), st>>>(L);
+    if (program_has_udf(q))
+      scan_kernel<kConsumers, true><<<grid, kThreads, smem_bytes(), st>>>(L);
+    else
+      scan_kernel<kConsumersLean, false><<<grid, kThreadsLean, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
       write_kernel<<<q.nunits, kWriteThreads, kWriteSmem, st>>>(L);
