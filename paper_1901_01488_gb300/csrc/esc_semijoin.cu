@@ -7,9 +7,10 @@
 // and on the host, for every dimension subset S,
 //   count(S) = sum over v that contain S of h[v]   (superset sum).
 //
-// Kernel shape: persistent grid of 2 blocks of 512 threads per SM; each
-// thread streams 8 rows per step with 16-byte non-allocating loads of every FK
-// column (4 rows per load).  The kernel is specialised on how many bitmaps
+// Kernel shape: persistent grid of 2 blocks of 512 threads per SM (shared
+// memory sized to the bitmaps it holds, the rest of the SM's on-chip memory
+// left to L1); each thread streams 8 rows per step with 16-byte
+// non-allocating loads of every FK column (4 rows per load).  The kernel is specialised on how many bitmaps
 // sit in shared memory (dimensions are ordered smallest bitmap first, so the
 // shared ones come first): each probe is then a fixed sequence -- clamp the
 // word index, load, shift, mask with the bounds test.  The 16 bins are 8-bit
@@ -172,6 +173,11 @@ cudaError_t launch_semijoin(const SjParams &P, size_t smem, int grid, cudaStream
   std::call_once(once[dev & 63], [&] {
     attr[dev & 63] = cudaFuncSetAttribute(semijoin_kernel<ND, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)kSjSmemBitmapBytes);
+    // as much L1 as the launch leaves: a bitmap probed in place (too large for
+    // shared memory) is then mostly served from L1 (its hot words: Zipf keys)
+    if (attr[dev & 63] == cudaSuccess)
+      attr[dev & 63] = cudaFuncSetAttribute(semijoin_kernel<ND, NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxL1);
   });
   if (attr[dev & 63] != cudaSuccess) return attr[dev & 63];
   semijoin_kernel<ND, NS><<<grid, kSjThreads, smem, st>>>(P);
