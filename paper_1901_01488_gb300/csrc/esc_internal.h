@@ -24,7 +24,7 @@ constexpr int kMaxDepth = 8;    // evaluation stack: 8 masks of 8 bits in one u6
 constexpr int kV = 8;           // rows per lane per group
 constexpr int kGroup = 256;     // rows per warp group (32 lanes x 8 rows)
 constexpr int kMaxTileRows = 32768;
-constexpr int kMaxUnitRows = 65536;   // rows per work unit (its masks stay in shared memory)
+constexpr int kMaxUnitRows = 65536;   // rows per scan work unit at most, and per compaction unit
 
 // Lane l of a warp owns, in a 256-row group, the rows
 //   64*j + 2*l + i   for j in 0..3, i in 0..1;
@@ -91,7 +91,7 @@ struct Query {
   uint32_t ngroups;       // 256-row groups: ceil(nrows / 256)
   uint32_t is_const;      // the program reads no column: no work units, answered by the constant kernel
   uint32_t const_value;   // its value (0 or 1) when is_const
-  uint32_t pad1;
+  uint32_t nwunits;       // compaction units: kMaxUnitRows rows each (write-kernel blocks, unit totals)
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

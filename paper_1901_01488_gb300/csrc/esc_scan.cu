@@ -19,7 +19,8 @@
 //  * counts: popc per lane, one atomic per warp and query;
 //  * ordered compaction, first pass: the selection bitmap (lane-major),
 //    staged per tile in shared memory and written with one bulk copy, and a
-//    total per work unit; second pass (write_kernel, one block per unit): a
+//    total per compaction unit of 65536 rows; second pass (write_kernel,
+//    one block per compaction unit): a
 //    decoupled look-back over the unit totals (Merrill & Garland,
 //    "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), a
 //    block scan of the group counts, then ids and projected values to
@@ -504,8 +505,7 @@ struct StageMeta {
   uint32_t tile;   // tile index within the query
   uint32_t rows;   // valid rows in this tile
   uint32_t dead;   // 1: the launch is aborting, skip the work (same for every reader)
-  uint32_t unit;   // unit index within the query
-  uint32_t pad[3];
+  uint32_t pad[4];
 };
 
 struct Launch {
@@ -664,7 +664,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           m.tile = tile;
           m.rows = rows;
           m.dead = dead;
-          m.unit = unit;
           mbar_arrive_expect_tx(&full_bar[s], tot);
         }
         __syncwarp();
@@ -685,15 +684,14 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
   unsigned long long *acc_ptr = nullptr;  // query count being accumulated
   int acc_q = -1;
   uint32_t acc = 0;                       // this lane's share
-  unsigned long long *uacc_ptr = nullptr; // unit total being accumulated (MODE_SELECT)
+  unsigned long long *uacc_ptr = nullptr; // compaction-unit total being accumulated (MODE_SELECT)
   uint32_t uacc = 0;
   while (true) {
     const bool got = mbar_wait(&full_bar[s], phase, hdr);
     const StageMeta mt = meta[s];
     const bool end = !got || mt.q < 0;
     const Query *Q = &qslot[s];
-    unsigned long long *uptr = (!end && Q->mode == MODE_SELECT) ? Q->unit_total + mt.unit : nullptr;
-    if (uacc_ptr && (end || uptr != uacc_ptr)) {
+    if (uacc_ptr && end) {
       const uint32_t t = __reduce_add_sync(FULL, uacc);
       if (lane == 0 && t) atomicAdd(uacc_ptr, (unsigned long long)t);
       uacc = 0;
@@ -717,7 +715,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
     const uint32_t r0 = mt.tile * Q->tile_rows;
     acc_q = mt.q;
     acc_ptr = Q->count;
-    uacc_ptr = uptr;
     // Consumers claim pairs of adjacent groups of the stage from a shared
     // counter until none is left, then move on to the next stage: the work of
     // a stage spreads over every consumer whatever its group count, and a warp
@@ -748,6 +745,17 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           if (mode == MODE_COUNT) continue;
           uint32_t word = 0;
           if (mode == MODE_SELECT) {
+            // the group's compaction unit (kMaxUnitGroups groups): flush the
+            // running total when it changes (warp-uniform)
+            unsigned long long *up = Q->unit_total + (mt.tile * Q->gmax + (uint32_t)gs[i]) / (uint32_t)kMaxUnitGroups;
+            if (up != uacc_ptr) {
+              if (uacc_ptr) {
+                const uint32_t t = __reduce_add_sync(FULL, uacc);
+                if (lane == 0 && t) atomicAdd(uacc_ptr, (unsigned long long)t);
+              }
+              uacc = 0;
+              uacc_ptr = up;
+            }
             uacc += c;
             // selection bitmap, lane-major: byte l of the group's 32 bytes is
             // lane l's mask (bit 2j+i: row 64*j + 2*l + i of the group); the
@@ -801,8 +809,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
 }
 
 // ------------------------------------------------------------------ the write kernel
-// Second pass of ordered compaction, one block per work unit (<= 65536 rows,
-// <= 256 groups of 256 rows: one thread per group).
+// Second pass of ordered compaction, one block per compaction unit
+// (kMaxUnitRows = 65536 rows, 256 groups of 256 rows: one thread per group;
+// independent of the scan's work units, so that a sparse selection runs as
+// few, full blocks whatever the predicate's read width).
 //  1. The unit's first output slot: a decoupled look-back over the units
 //     before it (Merrill & Garland 2016).  Every unit's aggregate is already
 //     final (written by the scan kernel), so the look-back adds aggregates
@@ -1044,7 +1054,7 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     }
   }
   const uint32_t u = blockIdx.x - Q->wunit_base;
-  const uint32_t urows = Q->unit_tiles * Q->tile_rows;
+  const uint32_t urows = kMaxUnitRows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
   const int ng = (int)((rows + kGroup - 1) / kGroup);
@@ -1308,7 +1318,6 @@ __global__ void __launch_bounds__(kThreads, 1) shared_kernel(const __grid_consta
           m.tile = tile;
           m.rows = rows;
           m.dead = dead;
-          m.unit = u;
           mbar_arrive_expect_tx(&full_bar[s], tot);
         }
         __syncwarp();
@@ -1544,6 +1553,7 @@ void mark_constant(Query &q) {
   q.is_const = 1;
   q.const_value = v;
   q.nunits = 0;
+  q.nwunits = 0;
   q.ntiles = 0;
 }
 
@@ -1578,12 +1588,10 @@ uint32_t tile_rows_for(const Query &q, const esc_tuning &tu) {
   return std::min<uint32_t>(std::min<uint32_t>(t, kMaxTileRows), tu.max_tile_rows);
 }
 
-// Stage layout (read columns back to back, each slice 128-byte aligned), and
-// the work units: consecutive tiles claimed with one ticket and, for ordered
-// compaction, resolved with one look-back.  Units hold at most ~512 KB of
-// staged columns and there are >= 8 per SM when the table is large enough,
-// which keeps the unit rate (look-backs per microsecond) low enough for the
-// look-back chain to keep up with HBM.
+// Stage layout (read columns back to back, each slice 128-byte aligned), the
+// work units (consecutive tiles claimed with one ticket: at most ~512 KB of
+// staged columns, >= 8 per SM when the table is large enough), and the
+// compaction units (kMaxUnitRows rows each, one write-kernel block).
 void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
   q.tile_rows = tile_rows_for(q, tu);
   uint32_t off = 0, bpr = 0;
@@ -1606,6 +1614,7 @@ void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
   const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * tu.units_per_sm);
   q.unit_tiles = std::min(std::max<uint32_t>(want, 1), max_ut);
   q.nunits = (q.ntiles + q.unit_tiles - 1) / q.unit_tiles;
+  q.nwunits = (uint32_t)(((uint64_t)q.nrows + kMaxUnitRows - 1) / kMaxUnitRows);
 }
 
 
@@ -1634,7 +1643,7 @@ esc_status launch_scan(const Launch &L, bool udf, cudaStream_t st) {
   return ESC_OK;
 }
 
-// Second pass of compaction: the write kernel, one block per work unit.
+// Second pass of compaction: the write kernel, one block per compaction unit.
 esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) {
   if (unit_blocks == 0) return ESC_OK;
   write_kernel<<<unit_blocks, kWriteThreads, kWriteSmem, st>>>(L);
@@ -1645,14 +1654,14 @@ esc_status launch_write(const Launch &L, uint32_t unit_blocks, cudaStream_t st) 
 // Compaction scratch of one query: unit totals and look-back words (both
 // zeroed before the scan), then the selection bitmap (the scan writes every
 // word before the write kernel reads it).
-size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nunits * 16 + 255) & ~(size_t)255; }
+size_t select_zeroed_bytes(const Query &q) { return ((size_t)q.nwunits * 16 + 255) & ~(size_t)255; }
 size_t select_other_bytes(const Query &q) {
   const size_t groups = (size_t)q.ntiles * q.gmax;
   return (groups * 32 + 255) & ~(size_t)255;
 }
 void select_bind(Query &q, uint8_t *zeroed, uint8_t *other) {
   q.unit_total = reinterpret_cast<unsigned long long *>(zeroed);
-  q.unit_status = q.unit_total + q.nunits;
+  q.unit_status = q.unit_total + q.nwunits;
   q.bitmap = reinterpret_cast<uint32_t *>(other);
 }
 
@@ -1728,7 +1737,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
     s = launch_const(L, cval, st);
   } else {
     s = launch_scan(L, program_has_udf(L.q0), st);
-    if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nunits, st);
+    if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nwunits, st);
   }
   if (s != ESC_OK) {
     cudaFreeAsync(mem, st);
@@ -1860,7 +1869,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     qs[i].wunit_base = (uint32_t)wunits;
     units += qs[i].nunits;
     if (compact) {
-      wunits += qs[i].nunits;
+      wunits += qs[i].nwunits;
       zeroed += select_zeroed_bytes(qs[i]);
       other += select_other_bytes(qs[i]);
     }
@@ -1908,7 +1917,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
-      init[i] = qs[i].nunits;                         // counted down by the write kernel
+      init[i] = qs[i].nwunits;                        // counted down by the write kernel
     } else {
       init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);  // counted down by the scan kernel
     }
@@ -2030,7 +2039,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
     qs[i].wunit_base = (uint32_t)wunits;
     units += qs[i].nunits;
     if (compact) {
-      wunits += qs[i].nunits;
+      wunits += qs[i].nwunits;
       zeroed += select_zeroed_bytes(qs[i]);
       other += select_other_bytes(qs[i]);
     }
@@ -2064,7 +2073,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       select_bind(qs[i], zp, op);
       zp += select_zeroed_bytes(qs[i]);
       op += select_other_bytes(qs[i]);
-      init[i] = qs[i].nunits;
+      init[i] = qs[i].nwunits;
     } else {
       init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);
     }
@@ -2337,7 +2346,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
       scan_kernel<kConsumersLean, false><<<grid, kThreadsLean, smem_bytes(), st>>>(L);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
-      write_kernel<<<q.nunits, kWriteThreads, kWriteSmem, st>>>(L);
+      write_kernel<<<q.nwunits, kWriteThreads, kWriteSmem, st>>>(L);
       ESC_CK(cudaGetLastError());
     }
   }
