@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
 constexpr int kWriteThreads = 256;
 constexpr int kWriteWarps = kWriteThreads / 32;
 static_assert(kMaxUnitGroups <= kWriteThreads, "one write-kernel thread per group of a unit");
-constexpr uint32_t kDenseMin = 97;       // qualifying rows of a group for the dense path
+constexpr uint32_t kDenseMin = 64;       // qualifying rows of a group for the dense path
 constexpr uint32_t kRawBytes = 2048;     // per warp: a dense group's projected values (<= 8 B per row at once)
 constexpr uint32_t kStageEntries = kRawBytes / 4;  // sparse entries staged per warp (same buffer)
 
