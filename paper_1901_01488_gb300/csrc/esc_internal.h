@@ -92,6 +92,8 @@ struct Query {
   uint32_t is_const;      // the program reads no column: no work units, answered by the constant kernel
   uint32_t const_value;   // its value (0 or 1) when is_const
   uint32_t nwunits;       // compaction units: kMaxUnitRows rows each (write-kernel blocks, unit totals)
+  uint32_t unit_big;      // work units 0..unit_big-1 hold unit_tiles tiles, the later ones one tile
+  uint32_t pad2[3];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

@@ -48,6 +48,7 @@ constexpr int kConsumersLean = 19;
 constexpr int kThreadsLean = 32 * (kConsumersLean + 1);
 constexpr int kStages = 3;
 constexpr uint32_t kStageBytes = 64 * 1024;
+constexpr int kTailTilesPerSm = 8;      // single-tile work units at the end of a query (per SM)
 constexpr int kMaxUnitGroups = kMaxUnitRows / kGroup;  // 256: one write-kernel thread per group
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr uint32_t FULL = 0xffffffffu;
@@ -500,6 +501,15 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
+// Tiles [t0, t1) of work unit u of a query: the first unit_big units hold
+// unit_tiles tiles each, the rest one tile each, so that the last work of a
+// launch comes in small pieces and the SMs finish together.
+__device__ __forceinline__ void unit_range(const Query &Q, uint32_t u, uint32_t &t0, uint32_t &t1) {
+  const uint32_t nb = Q.unit_big, ut = Q.unit_tiles;
+  t0 = u < nb ? u * ut : nb * ut + (u - nb);
+  t1 = min(u < nb ? t0 + ut : t0 + 1u, Q.ntiles);
+}
+
 struct StageMeta {
   int32_t q;       // query index, -1 = end of work
   uint32_t tile;   // tile index within the query
@@ -612,9 +622,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       while (qc + 1 < L.nq && u >= query_ptr(L, qc + 1)->unit_base) ++qc;
       const Query *Qg = query_ptr(L, qc);
       const uint32_t unit = u - Qg->unit_base;
-      const uint32_t ut = Qg->unit_tiles;
-      const uint32_t t0 = unit * ut;
-      const uint32_t t1 = min(t0 + ut, Qg->ntiles);
+      uint32_t t0, t1;
+      unit_range(*Qg, unit, t0, t1);
       for (uint32_t tile = t0; tile < t1; ++tile) {
         if (!mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true)) {
           done = true;
@@ -1277,8 +1286,8 @@ __global__ void __launch_bounds__(kThreads, 1) shared_kernel(const __grid_consta
         }
         break;
       }
-      const uint32_t t0 = u * Y.unit_tiles;
-      const uint32_t t1 = min(t0 + Y.unit_tiles, Y.ntiles);
+      uint32_t t0, t1;
+      unit_range(Y, u, t0, t1);
       for (uint32_t tile = t0; tile < t1; ++tile) {
         if (!mbar_wait(&empty_bar[s], phase ^ 1u, hdr, kWaitLimitNs, true)) {
           done = true;
@@ -1613,7 +1622,10 @@ void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
       1, std::min<uint64_t>((uint64_t)tu.max_unit_kb * 1024 / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
   const uint32_t want = q.ntiles / (uint32_t)std::max(1, sms * tu.units_per_sm);
   q.unit_tiles = std::min(std::max<uint32_t>(want, 1), max_ut);
-  q.nunits = (q.ntiles + q.unit_tiles - 1) / q.unit_tiles;
+  // the last kTailTilesPerSm tiles per SM go out one tile per unit
+  const uint32_t tail = std::min<uint32_t>(q.ntiles, (uint32_t)(kTailTilesPerSm * sms));
+  q.unit_big = (q.ntiles - tail) / q.unit_tiles;
+  q.nunits = q.unit_big + (q.ntiles - q.unit_big * q.unit_tiles);
   q.nwunits = (uint32_t)(((uint64_t)q.nrows + kMaxUnitRows - 1) / kMaxUnitRows);
 }
 
