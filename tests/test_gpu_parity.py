@@ -75,6 +75,24 @@ def test_random_predicates_all_types(esc):
     assert done > 120
 
 
+def test_in_set_forms(esc):
+    """IN lists: the 256-bit set of values 0..255 and the general list, on
+    every column type (negative and out-of-range column values included):
+    word boundaries of the set (31/32, 63/64, 255), negative and repeated
+    values, negation, and use inside AND/OR."""
+    host = host_table(100_003, seed=31)
+    tbl = esc.Table(as_columns(host, "cuda"), 100_003)
+    lists = ["0", "31", "32", "63", "64", "0, 3, 31", "1, 33, 63", "32, 40, 47", "0, 31, 32, 63",
+             "5, 64, 200", "63, 64", "255", "0, 255", "-1, 0, 1, 31", "2, 2, 2"]
+    n = 0
+    for col in ("a", "b", "c", "d", "e"):
+        for lst in lists:
+            for text in (f"{col} IN ({lst})", f"NOT {col} IN ({lst})",
+                         f"({col} IN ({lst}) OR a = 7) AND b IN ({lst})"):
+                n += _check(esc, host, tbl, text, ("a", "b"))
+    assert n > 0
+
+
 def test_truncation(esc):
     t = datagen.single_table(50_000, seed=7, device="cuda")
     host = t.host()
