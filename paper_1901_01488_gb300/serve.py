@@ -18,7 +18,7 @@ from __future__ import annotations
 import dataclasses
 import time
 from collections import deque
-from typing import Deque, Dict, List, Optional, Sequence
+from typing import Callable, Deque, Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 import torch
@@ -38,13 +38,47 @@ class Request:
 
 
 def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
-    """Device memory a request holds while in flight: library scratch for
-    materialisation (the selection bitmap, 1/8 byte per row, and 16 bytes
-    per work unit of at least 2048 rows) and its output buffers."""
+    """Device memory a request holds while in flight: its compiled query and
+    counters in the launch (4 KB), and when it materialises, the library's
+    scratch (the selection bitmap, 1/8 byte per row rounded up to whole tiles
+    of at most 32768 rows, 16 bytes per compaction unit of 65536 rows,
+    headers) and its output buffers."""
+    base = 4096
     if not req.proj:
-        return 256
-    scratch = nrows // 8 + nrows // 128 + 4096
-    return scratch + req.capacity * (4 + sum(widths[c] for c in req.proj))
+        return base
+    scratch = nrows // 8 + 16 * ((nrows + 65535) // 65536) + 8192
+    return base + scratch + req.capacity * (4 + sum(widths[c] for c in req.proj))
+
+
+def admit(pending: Deque[Request], in_flight: int, budget: int, max_batch: int,
+          size: Callable[[Request], int]) -> Tuple[List[Request], int]:
+    """The next wave: requests from the front of `pending`, in arrival order,
+    while the wave holds fewer than `max_batch` and its bytes fit the budget
+    beside those in flight.  A request larger than the whole budget runs
+    alone once nothing else is in flight.  Returns (wave, its bytes)."""
+    batch: List[Request] = []
+    nbytes = 0
+    while pending and len(batch) < max_batch:
+        b = size(pending[0])
+        alone = not batch and in_flight == 0
+        if in_flight + nbytes + b > budget and not alone:
+            break
+        batch.append(pending.popleft())
+        nbytes += b
+    return batch, nbytes
+
+
+def wave_groups(batch: Sequence[Request], shared_min: int) -> Tuple[List[List[Request]], List[Request]]:
+    """Splits a wave into shared passes (the count requests of one table, when
+    at least `shared_min` of them are in the wave; tables in order of their
+    first request, requests in arrival order) and the rest, run as one batch."""
+    per_table: Dict[int, List[Request]] = {}
+    for r in batch:
+        if not r.proj:
+            per_table.setdefault(r.table, []).append(r)
+    groups = [rs for rs in per_table.values() if len(rs) >= shared_min]
+    shared = {id(r) for rs in groups for r in rs}
+    return groups, [r for r in batch if id(r) not in shared]
 
 
 class Server:
@@ -89,17 +123,9 @@ class Server:
                     slots[k] = None
                     progressed = True
                 if slots[k] is None and pending:
-                    batch, nbytes = [], 0
-                    while pending and len(batch) < self.max_batch:
-                        r = pending[0]
-                        b = request_bytes(self.tables[r.table].nrows, r, self.widths[r.table])
-                        # admission by device memory; a request larger than the
-                        # whole budget runs alone once nothing else is in flight
-                        alone = not batch and self.in_flight_bytes == 0
-                        if self.in_flight_bytes + nbytes + b > self.budget and not alone:
-                            break
-                        batch.append(pending.popleft())
-                        nbytes += b
+                    batch, nbytes = admit(pending, self.in_flight_bytes, self.budget, self.max_batch,
+                                          lambda r: request_bytes(self.tables[r.table].nrows, r,
+                                                                  self.widths[r.table]))
                     if batch:
                         self._launch(batch, k, st, nbytes, slots)
                         progressed = True
@@ -109,15 +135,10 @@ class Server:
 
     def _launch(self, batch: List[Request], k: int, st, nbytes: int, slots) -> None:
         esc = self.esc
-        # count requests on one table, when there are enough of them, share one
-        # pass over it; the rest run as one batch.  Shared groups come first.
-        per_table: Dict[int, List[Request]] = {}
-        for r in batch:
-            if not r.proj:
-                per_table.setdefault(r.table, []).append(r)
-        shared = {ti for ti, rs in per_table.items() if len(rs) >= self.shared_min}
-        batch = ([r for r in batch if not r.proj and r.table in shared] +
-                 [r for r in batch if r.proj or r.table not in shared])
+        # shared passes first (one per table), then the rest as one batch
+        groups, rest_reqs = wave_groups(batch, self.shared_min)
+        batch = [r for g in groups for r in g] + rest_reqs
+        nshared = len(batch) - len(rest_reqs)
         preds = []
         rows = []
         for r in batch:
@@ -132,14 +153,13 @@ class Server:
         counts = torch.zeros(len(batch), dtype=torch.int64, device=self.device)
         with torch.cuda.stream(st):
             i = 0
-            while i < len(batch) and not batch[i].proj and batch[i].table in shared:
-                j = i
-                while j < len(batch) and not batch[j].proj and batch[j].table == batch[i].table:
-                    j += 1
-                esc.esc_selectivity_shared_async(self.tables[batch[i].table].handle, [p.handle for p in preds[i:j]],
+            for g in groups:
+                j = i + len(g)
+                esc.esc_selectivity_shared_async(self.tables[g[0].table].handle, [p.handle for p in preds[i:j]],
                                                  counts[i:j], st)
                 self.shared_launches += 1
                 i = j
+            assert i == nshared
             if i < len(batch):
                 rest = rows[i:]
                 esc.esc_selectivity_batch_async([self.tables[r.table].handle for r in batch[i:]],
