@@ -126,10 +126,11 @@ esc_status esc_predicate_destroy(esc_pred *pred);
 /* Launch shape of a compiled predicate's scans (the autotuner's knobs; not
  * in the paper).  max_tile_rows: rows staged per tile (256..32768, a
  * multiple of 256; the stage size caps it further); max_unit_kb: staged
- * bytes per work unit (16..4096; a unit is claimed with one ticket and is the
- * granularity of the compaction offsets); units_per_sm: work units to aim
- * for per SM (1..64; more balances load, fewer amortises per-unit work).
- * Defaults: 32768, 512, 8.  Results never depend on these. */
+ * bytes per work unit (16..4096; a unit is a run of tiles claimed with one
+ * ticket; the last tiles of a table always go out one per unit);
+ * units_per_sm: work units to aim for per SM (1..64; more balances load,
+ * fewer amortises per-unit work).  Defaults: 32768, 512, 8.  Results never
+ * depend on these. */
 typedef struct esc_tuning {
     uint32_t max_tile_rows;
     uint32_t max_unit_kb;

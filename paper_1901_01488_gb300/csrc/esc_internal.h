@@ -88,12 +88,11 @@ struct Query {
   uint8_t ref_w[kMaxRef];         // element width of each read column
   uint8_t proj_w[kMaxProj];
   int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
-  uint32_t ngroups;       // 256-row groups: ceil(nrows / 256)
   uint32_t is_const;      // the program reads no column: no work units, answered by the constant kernel
   uint32_t const_value;   // its value (0 or 1) when is_const
   uint32_t nwunits;       // compaction units: kMaxUnitRows rows each (write-kernel blocks, unit totals)
   uint32_t unit_big;      // work units 0..unit_big-1 hold unit_tiles tiles, the later ones one tile
-  uint32_t pad2[3];
+  uint32_t pad2[4];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

@@ -521,7 +521,7 @@ struct StageMeta {
 struct Launch {
   const Query *queries;  // device array of nq queries, or null: use q0
   int32_t nq;
-  uint32_t total_units;  // scan kernel: work units; write kernel: blocks
+  uint32_t total_units;  // work units (scan tickets) of all queries
   ScratchHdr *hdr;
   uint32_t pad[4];
   Query q0;
@@ -896,11 +896,9 @@ __device__ __forceinline__ int block_query(const Launch &L, F base) {
 struct GatherInfo {
   uint64_t capacity;
   uint32_t *out_ids;
-  const uint32_t *bitmap;
-  const unsigned long long *goff;
   unsigned int *tiles_left;
   unsigned long long *done_ns;
-  uint32_t ngroups, nrows;
+  uint32_t nrows;
   int32_t nproj;
   uint8_t proj_w[kMaxProj];
   const uint8_t *proj_ptr[kMaxProj];
@@ -1049,10 +1047,8 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     if (lane == 0) {
       G.capacity = Q->capacity;
       G.out_ids = Q->out_ids;
-      G.bitmap = Q->bitmap;
       G.tiles_left = Q->tiles_left;
       G.done_ns = Q->done_ns;
-      G.ngroups = Q->ngroups;
       G.nrows = Q->nrows;
       G.nproj = np;
     }
@@ -1616,7 +1612,6 @@ void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
   }
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;
   q.gmax = q.tile_rows / kGroup;
-  q.ngroups = (q.nrows + kGroup - 1) / kGroup;
   const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);
   const uint32_t max_ut = (uint32_t)std::max<uint64_t>(
       1, std::min<uint64_t>((uint64_t)tu.max_unit_kb * 1024 / tile_bytes, (uint64_t)kMaxUnitRows / q.tile_rows));
