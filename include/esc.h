@@ -123,6 +123,17 @@ esc_status esc_predicate_compile(const esc_table *table, const char *text,
                                  const char *const *proj, int32_t nproj, esc_pred **out);
 esc_status esc_predicate_destroy(esc_pred *pred);
 
+/* Compiles n predicates against one table, as esc_predicate_compile does for
+ * each (same projection for all), on up to `nthreads` host threads
+ * (<= 0: one per hardware thread; at least 64 predicates per thread).
+ * out: host array of n handles, each released with esc_predicate_destroy.
+ * If any text fails, every handle is released, out[] is all NULL, and the
+ * status is that of the failing predicate of lowest index, whose index the
+ * message names. */
+esc_status esc_predicate_compile_many(const esc_table *table, const char *const *texts, int32_t n,
+                                      const char *const *proj, int32_t nproj, esc_pred **out,
+                                      int32_t nthreads);
+
 /* Launch shape of a compiled predicate's scans (the autotuner's knobs; not
  * in the paper).  max_tile_rows: rows staged per tile (256..32768, a
  * multiple of 256; the stage size caps it further); max_unit_kb: staged

@@ -22,6 +22,7 @@
 #include <new>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "esc_internal.h"
@@ -930,6 +931,57 @@ esc_status esc_predicate_get_tuning(const esc_pred *p, esc_tuning *out) {
 
 esc_status esc_predicate_destroy(esc_pred *p) {
   delete p;
+  return ESC_OK;
+}
+
+esc_status esc_predicate_compile_many(const esc_table *t, const char *const *texts, int32_t n,
+                                      const char *const *proj, int32_t nproj, esc_pred **out, int32_t nthreads) {
+  if (n < 0 || (n > 0 && (!texts || !out)))
+    return fail(ESC_EINVAL, "esc_predicate_compile_many: bad arguments");
+  for (int32_t i = 0; i < n; ++i) out[i] = nullptr;
+  if (n == 0) {
+    clear_error();
+    return ESC_OK;
+  }
+  // contiguous ranges of at least 64 predicates per thread; the compiler has
+  // no shared mutable state (its error message is per thread)
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  int nt = nthreads > 0 ? nthreads : hw;
+  nt = std::max(1, std::min({nt, 64, std::max(1, (int)(n / 64))}));
+  std::vector<esc_status> st((size_t)nt, ESC_OK);
+  std::vector<int32_t> bad((size_t)nt, -1);
+  std::vector<std::string> msg((size_t)nt);
+  auto work = [&](int k) {
+    const int32_t i0 = (int32_t)((int64_t)n * k / nt), i1 = (int32_t)((int64_t)n * (k + 1) / nt);
+    for (int32_t i = i0; i < i1; ++i) {
+      const esc_status s = esc_predicate_compile(t, texts[i], proj, nproj, &out[i]);
+      if (s != ESC_OK) {
+        st[(size_t)k] = s;
+        bad[(size_t)k] = i;
+        msg[(size_t)k] = esc_last_error();
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  int started = 1;
+  try {
+    for (; started < nt; ++started) pool.emplace_back(work, started);
+  } catch (...) {  // no more threads: the rest of the ranges run here
+  }
+  work(0);
+  for (int k = started; k < nt; ++k) work(k);
+  for (auto &th : pool) th.join();
+  for (int k = 0; k < nt; ++k) {
+    if (st[(size_t)k] == ESC_OK) continue;
+    for (int32_t i = 0; i < n; ++i) {
+      delete out[i];
+      out[i] = nullptr;
+    }
+    return fail(st[(size_t)k], "esc_predicate_compile_many: predicate " + std::to_string(bad[(size_t)k]) + ": " +
+                                   msg[(size_t)k]);
+  }
+  clear_error();
   return ESC_OK;
 }
 

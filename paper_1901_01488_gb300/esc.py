@@ -52,6 +52,9 @@ _sig = {
     "esc_predicate_compile": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int32,
                                ctypes.POINTER(_P)], _S),
     "esc_predicate_destroy": ([_P], _S),
+    "esc_predicate_compile_many": ([_P, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_char_p), ctypes.c_int32, ctypes.POINTER(_P),
+                                    ctypes.c_int32], _S),
     "esc_predicate_explain": ([_P, ctypes.c_char_p, ctypes.c_uint64], _S),
     "esc_predicate_set_tuning": ([_P, ctypes.POINTER(esc_tuning)], _S),
     "esc_predicate_get_tuning": ([_P, ctypes.POINTER(esc_tuning)], _S),
@@ -134,6 +137,18 @@ def esc_predicate_compile(table: int, text: str, proj: Sequence[str] = ()) -> in
 
 def esc_predicate_destroy(pred: int) -> None:
     _lib.esc_predicate_destroy(pred)
+
+
+def esc_predicate_compile_many(table: int, texts: Sequence[str], proj: Sequence[str] = (),
+                               threads: int = 0) -> List[int]:
+    """Handles of the compiled texts (the caller destroys each)."""
+    n = len(texts)
+    arr = (ctypes.c_char_p * max(1, n))(*[t.encode() for t in texts])
+    names = (ctypes.c_char_p * max(1, len(proj)))(*[p.encode() for p in proj])
+    out = (_P * max(1, n))()
+    _check(_lib.esc_predicate_compile_many(table, arr, n, names, len(proj), out, threads),
+           "esc_predicate_compile_many")
+    return [out[i] for i in range(n)]
 
 
 def esc_predicate_explain(pred: int) -> str:
@@ -391,6 +406,30 @@ class Predicate:
         if self.handle:
             esc_predicate_destroy(self.handle)
             self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PredicateSet:
+    """Many predicates compiled against one Table in one call (host threads),
+    with one projection; `handles` in the order of the texts."""
+
+    def __init__(self, table: Table, texts: Sequence[str], proj: Sequence[str] = (), threads: int = 0):
+        self.table = table
+        self.proj = tuple(proj)
+        self.handles = esc_predicate_compile_many(table.handle, list(texts), self.proj, threads)
+
+    def __len__(self) -> int:
+        return len(self.handles)
+
+    def close(self):
+        for h in self.handles:
+            esc_predicate_destroy(h)
+        self.handles = []
 
     def __del__(self):
         try:

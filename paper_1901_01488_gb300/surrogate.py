@@ -88,14 +88,15 @@ def qerror(est: np.ndarray, true: np.ndarray) -> np.ndarray:
 
 
 def exact_counts(esc, table, preds: Sequence[datagen.Predicate], chunk: int = 2048, stream=None) -> np.ndarray:
-    """Exact ESC counts of many predicates on one table: one shared pass per
-    chunk (esc_selectivity_shared_async), counts read back once at the end."""
+    """Exact ESC counts of many predicates on one table: each chunk compiled
+    in one call (host threads), one shared pass per chunk
+    (esc_selectivity_shared_async), counts read back once at the end."""
     n = len(preds)
     dev = torch.zeros(max(1, n), dtype=torch.int64, device="cuda")
     keep = []
     for s in range(0, n, chunk):
-        ps = [esc.Predicate(table, p.text) for p in preds[s:s + chunk]]
-        esc.esc_selectivity_shared_async(table.handle, [p.handle for p in ps], dev[s:s + len(ps)], stream=stream)
+        ps = esc.PredicateSet(table, [p.text for p in preds[s:s + chunk]])
+        esc.esc_selectivity_shared_async(table.handle, ps.handles, dev[s:s + len(ps)], stream=stream)
         keep.append(ps)  # predicates stay alive until their pass has run
     out = dev[:n].cpu().numpy().astype(np.int64)
     return out

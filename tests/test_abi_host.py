@@ -225,3 +225,35 @@ def test_udf_magic_divides_exactly(esc):
             t = (mult * n) >> 64
             q = (t + ((n - t) >> s1)) >> s2
             assert q == n // d, (d, n)
+
+
+def test_compile_many_matches_single_compiles(esc):
+    """esc_predicate_compile_many: the same program as one compile per text
+    (on several threads), and on a bad text every handle released and the
+    lowest failing index named."""
+    cols = host_table(4096, seed=9)
+    t = _table(esc, cols)
+    texts = [x for x in random_preds(600, seed=12)]
+    good = []
+    for x in texts:
+        try:
+            p = esc.Predicate(t, x, ("b", "c"))
+            good.append((x, p.explain()))
+            p.close()
+        except esc.EscError:
+            pass
+    assert len(good) > 400
+    for threads in (1, 3, 0):
+        hs = esc.esc_predicate_compile_many(t.handle, [x for x, _ in good], ("b", "c"), threads)
+        assert [esc.esc_predicate_explain(h) for h in hs] == [e for _, e in good]
+        for h in hs:
+            esc.esc_predicate_destroy(h)
+    bad = [x for x, _ in good[:300]]
+    bad[170] = "b < "
+    bad[250] = "nosuchcolumn = 1"
+    with pytest.raises(esc.EscError, match="predicate 170"):
+        esc.esc_predicate_compile_many(t.handle, bad, (), 4)
+    assert esc.esc_predicate_compile_many(t.handle, [], ()) == []
+    ps = esc.PredicateSet(t, ["a < 3", "b IN (1, 2)"], ("a",))
+    assert len(ps) == 2 and all(ps.handles)
+    ps.close()
