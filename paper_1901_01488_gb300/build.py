@@ -4,6 +4,7 @@ Usage: python -m paper_1901_01488_gb300.build [--force]
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import subprocess
 import sys
@@ -50,10 +51,23 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    """Compiles what is out of date and links libesc.so; processes that build
+    at the same time (one per GPU under torchrun) take turns on a file lock,
+    so the later ones find everything up to date."""
     os.makedirs(OBJ, exist_ok=True)
+    with open(os.path.join(OBJ, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose_ptxas)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose_ptxas: bool) -> str:
     if force:
         for f in os.listdir(OBJ):
-            os.remove(os.path.join(OBJ, f))
+            if f.endswith(".o"):
+                os.remove(os.path.join(OBJ, f))
     with ThreadPoolExecutor(len(CU) + len(CPP)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), CU + CPP))
     if force or _stale(LIB, objs):
