@@ -8,7 +8,8 @@
 //  * scan_kernel, persistent: one CTA per SM, 1 producer warp + kConsumers
 //    consumer warps (kConsumersLean in the instance for programs without a
 //    udf, whose register demand is lower); work units (a few consecutive
-//    tiles) are claimed in order from a global ticket;
+//    tiles; the last tiles of a query one per unit) are claimed in order
+//    from a global ticket;
 //  * the producer stages every column the predicate reads into shared memory
 //    with 1-D bulk TMA copies (cp.async.bulk ... mbarrier::complete_tx) into a
 //    ring of kStages stages; the ragged tail of the last tile (< 16 bytes per
@@ -20,11 +21,10 @@
 //  * ordered compaction, first pass: the selection bitmap (lane-major),
 //    staged per tile in shared memory and written with one bulk copy, and a
 //    total per compaction unit of 65536 rows; second pass (write_kernel,
-//    one block per compaction unit): a
-//    decoupled look-back over the unit totals (Merrill & Garland,
-//    "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), a
-//    block scan of the group counts, then ids and projected values to
-//    consecutive output slots.
+//    one block per compaction unit): a decoupled look-back over the unit
+//    totals (Merrill & Garland, "Single-pass Parallel Prefix Scan with
+//    Decoupled Look-back", 2016), a block scan of the group counts, then ids
+//    and projected values to consecutive output slots.
 // Every wait on an mbarrier is bounded by %globaltimer; on expiry the kernel
 // records ESC_ETIMEOUT in the scratch header and all CTAs wind down.
 #include <cuda_runtime.h>
