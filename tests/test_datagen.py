@@ -59,3 +59,28 @@ def test_predicates_parse_and_are_seeded():
     for p in ps:
         oracle.parse(p.text)
         assert 1 <= len(p.terms) <= 6
+
+
+def test_zipf_sampling_matches_the_law():
+    """Keys drawn by inverse CDF follow P(rank r) = r^-s / H(n, s): the top
+    ranks one by one, and rank buckets [2^k, 2^(k+1)), within 5 sigma of the
+    binomial count; the key map is a bijection (exhaustive on a small n)."""
+    import math
+    n, s, count, salt = 1 << 24, 1.1, 2_000_000, 777
+    keys = datagen.zipf_keys(7, 0, 0, count, s, n, "cpu", salt=salt).numpy().astype(np.int64)
+    inv = pow(datagen.ZIPF_MULT, -1, n)
+    rank = ((keys - salt % n) % n * inv) % n + 1              # 1-based ranks
+    h = sum(r ** -s for r in range(1, 2_000_001)) + ((n + 0.5) ** (1 - s) - (2_000_000.5) ** (1 - s)) / (1 - s)
+    for r in range(1, 9):                                    # the head, rank by rank
+        p = r ** -s / h
+        got = np.count_nonzero(rank == r)
+        assert abs(got - count * p) < 5 * math.sqrt(count * p * (1 - p)), (r, got, count * p)
+    for k in range(0, 24, 3):                                # buckets of ranks
+        lo, hi = 1 << k, 1 << (k + 1)
+        p = sum(r ** -s for r in range(lo, min(hi, 200_000))) / h if hi <= 200_000 else \
+            ((hi - 0.5) ** (1 - s) - (lo - 0.5) ** (1 - s)) / (1 - s) / h
+        got = np.count_nonzero((rank >= lo) & (rank < hi))
+        assert abs(got - count * p) < 5 * math.sqrt(count * p * (1 - p)) + 1e-4 * count, (k, got, count * p)
+    small = 1000 if math.gcd(datagen.ZIPF_MULT, 1000) == 1 else 1001
+    ks = datagen.zipf_key_of_rank(torch.arange(small), small, salt).numpy()
+    assert sorted(ks.tolist()) == list(range(small))
