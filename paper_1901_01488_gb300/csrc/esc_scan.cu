@@ -2343,8 +2343,13 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
   if (mode == MODE_SELECT) select_bind(q, d->scratch + head, d->scratch + head + zeroed);
   uint32_t cval = 0;
   if (program_constant(q, &cval)) {
-    esc_status cs = launch_const(L, cval, st);
-    if (cs != ESC_OK) return cs;
+    // launched here rather than through launch_const, which would set up the
+    // library's memory pool on first use
+    const uint64_t work = (mode == MODE_SELECT && cval) ? std::min<uint64_t>(q.nrows, q.capacity) : 0;
+    const uint32_t grid =
+        (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d->sms * 8, (work + 255) / 256));
+    const_kernel<<<grid, 256, 0, st>>>(L, cval);
+    ESC_CK(cudaGetLastError());
   } else if (L.total_units > 0) {
     const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), L.total_units);
     if (program_has_udf(q))

@@ -358,16 +358,15 @@ def _range_term(rng: _Rng, col: str, s: float) -> Term:
     return Term("range", col, a, a + width - 1, est=width / d)
 
 
-def _eq_term(rng: _Rng, s: float) -> Term:
-    cands = ["code7", "code25", "code150", "qty"]
+def _eq_term(rng: _Rng, s: float, cands: Sequence[str]) -> Term:
     best = min(cands, key=lambda c: abs(math.log(max(s, 1e-12)) -
                                         math.log(1.0 / (SKEWED_SCHEMA[c][2] - SKEWED_SCHEMA[c][1] + 1))))
     _, lo, hi = SKEWED_SCHEMA[best]
     return Term("eq", best, rng.randint(lo, hi), est=1.0 / (hi - lo + 1))
 
 
-def _in_term(rng: _Rng, s: float) -> Term:
-    col = rng.choice(["code25", "code150", "code7"])
+def _in_term(rng: _Rng, s: float, cands: Sequence[str]) -> Term:
+    col = rng.choice(cands)
     _, lo, hi = SKEWED_SCHEMA[col]
     k = hi - lo + 1
     n = max(2, min(16, k, int(round(s * k))))
@@ -382,9 +381,8 @@ def _udf_term(rng: _Rng, s: float) -> Term:
     return Term("udf", "price", lo=k, est=(m - 1 - k) / m)
 
 
-def _or_term(rng: _Rng, s: float) -> Term:
+def _or_term(rng: _Rng, s: float, cols: Sequence[str]) -> Term:
     part = 1.0 - math.sqrt(max(0.0, 1.0 - min(s, 1.0)))
-    cols = ["day", "price", "qty", "code150", "key2"]
     c1 = rng.choice(cols)
     c2 = rng.choice([c for c in cols if c != c1])
     a = _range_term(rng, c1, part)
@@ -394,39 +392,73 @@ def _or_term(rng: _Rng, s: float) -> Term:
     return Term("or", parts=(a, b), est=a.est + b.est - a.est * b.est)
 
 
+# Columns a term reads (a udf reads price and qty; an OR pair both of its columns).
+def _term_columns(t: Term) -> Tuple[str, ...]:
+    if t.kind == "udf":
+        return ("price", "qty")
+    if t.kind == "or":
+        return tuple(c for p in t.parts for c in _term_columns(p))
+    return (t.col,)
+
+
 def random_predicate(seed: int, target: float, max_terms: int = 6) -> Predicate:
     """A conjunction of 1..max_terms terms aimed at selectivity `target`.
 
-    Non-driver terms are drawn first; the driver range on `price`, `day` or a
-    key column is then sized so that the product of aimed selectivities equals
-    the target.  Aims assume independent, uniform (or Zipf-known) columns; the
-    achieved selectivity is whatever the exact count says.
+    The driver column (`price`, `day` or `key`; not `day` below a target of
+    2e-3) is drawn first; the
+    other terms are drawn on columns no earlier term reads, so that no two
+    terms of the conjunction test the same column (two independent draws on
+    one column are mostly disjoint, a contradiction that reads nothing).  The
+    driver range is then sized so that the product of aimed selectivities
+    equals the target.  Aims assume independent, uniform (or Zipf-known)
+    columns; the achieved selectivity is whatever the exact count says (the
+    correlated code columns make it differ).  A term kind whose columns are
+    all taken, or whose coarse aim falls below the target, is replaced by a
+    range on a free column, or dropped.
     """
     rng = _Rng(seed)
     nterms = rng.randint(1, max_terms)
+    # `day` has 2,557 values: it cannot aim below 1/2557 alone
+    driver_col = rng.choice(["price", "price", "day", "key"] if target >= 2e-3 else ["price", "price", "key"])
+    used = {driver_col}
     others: List[Term] = []
-    logt = math.log(target)
+    rem = math.log(target)      # log of the selectivity budget the terms drawn so far leave
+
+    def free(cols):
+        return [c for c in cols if c not in used]
+
     for _ in range(nterms - 1):
         kind = rng.choice(["eq", "range", "in", "or", "udf"])
-        # spend a random share of the remaining selectivity budget (never below the target)
+        # spend a random share (up to half) of the remaining selectivity budget
         frac = rng.uniform() * 0.5
-        s = math.exp(logt * frac) if logt < 0 else 1.0
-        if kind == "eq":
-            t = _eq_term(rng, s)
-        elif kind == "range":
-            t = _range_term(rng, rng.choice(["day", "qty", "code150", "key", "key2"]), s)
-        elif kind == "in":
-            t = _in_term(rng, s)
-        elif kind == "or":
-            t = _or_term(rng, s)
-        else:
+        s = math.exp(rem * frac) if rem < 0 else 1.0
+        if kind == "eq" and free(["code7", "code25", "code150", "qty"]):
+            t = _eq_term(rng, s, free(["code7", "code25", "code150", "qty"]))
+        elif kind == "in" and free(["code25", "code150", "code7"]):
+            t = _in_term(rng, s, free(["code25", "code150", "code7"]))
+        elif kind == "or" and len(free(["day", "price", "qty", "code150", "key2"])) >= 2:
+            t = _or_term(rng, s, free(["day", "price", "qty", "code150", "key2"]))
+        elif kind == "udf" and not ({"price", "qty"} & used):
             t = _udf_term(rng, s)
+        elif free(["day", "qty", "code150", "key", "key2"]):
+            t = _range_term(rng, rng.choice(free(["day", "qty", "code150", "key", "key2"])), s)
+        else:
+            continue
+        if t.est < math.exp(rem) and t.kind != "range":
+            # a code test is coarse (1/7 of the rows at most for an equality):
+            # where it would spend more than the whole remaining budget, a
+            # range sized to the share takes its place
+            if not free(["day", "qty", "code150", "key", "key2"]):
+                continue
+            t = _range_term(rng, rng.choice(free(["day", "qty", "code150", "key", "key2"])), s)
+        used.update(_term_columns(t))
         others.append(t)
+        rem = min(0.0, rem - math.log(max(t.est, 1e-300)))
     prod = 1.0
     for t in others:
         prod *= t.est
     driver_s = min(1.0, target / prod) if prod > 0 else 1.0
-    driver = _range_term(rng, rng.choice(["price", "price", "day", "key"]), driver_s)
+    driver = _range_term(rng, driver_col, driver_s)
     terms = [driver] + others
     order = list(range(len(terms)))
     for i in range(len(order) - 1, 0, -1):          # Fisher-Yates on the term order

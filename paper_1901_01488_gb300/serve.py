@@ -141,17 +141,19 @@ class Server:
         nshared = len(batch) - len(rest_reqs)
         preds = []
         rows = []
-        for r in batch:
-            t = self.tables[r.table]
-            p = esc.Predicate(t, r.text, tuple(r.proj))
-            preds.append(p)
-            if r.proj:
-                r.rows = p.alloc_rows(max(1, r.capacity), device=self.device)
-                rows.append(r.rows)
-            else:
-                rows.append(None)
-        counts = torch.zeros(len(batch), dtype=torch.int64, device=self.device)
         with torch.cuda.stream(st):
+            # outputs and counts are allocated (and zeroed) on the wave's own
+            # stream, so that the kernels below are ordered after the fill
+            for r in batch:
+                t = self.tables[r.table]
+                p = esc.Predicate(t, r.text, tuple(r.proj))
+                preds.append(p)
+                if r.proj:
+                    r.rows = p.alloc_rows(max(1, r.capacity), device=self.device)
+                    rows.append(r.rows)
+                else:
+                    rows.append(None)
+            counts = torch.zeros(len(batch), dtype=torch.int64, device=self.device)
             i = 0
             for g in groups:
                 j = i + len(g)

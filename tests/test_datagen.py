@@ -84,3 +84,15 @@ def test_zipf_sampling_matches_the_law():
     small = 1000 if math.gcd(datagen.ZIPF_MULT, 1000) == 1 else 1001
     ks = datagen.zipf_key_of_rank(torch.arange(small), small, salt).numpy()
     assert sorted(ks.tolist()) == list(range(small))
+
+
+def test_headline_predicates_test_each_column_once():
+    """No two terms of a headline predicate read the same column (two draws
+    on one column would mostly be disjoint: a contradiction that reads no
+    column at all once compiled), and the generator's aim stays within two
+    decades of every target."""
+    import math
+    for p in datagen.skewed_predicates(200):
+        cols = [c for t in p.terms for c in datagen._term_columns(t)]
+        assert len(cols) == len(set(cols)), p.text
+        assert abs(math.log10(p.est / p.target)) < 2.0, p.text

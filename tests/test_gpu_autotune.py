@@ -45,3 +45,52 @@ def test_autotuner_caches_choices(tmp_path):
         assert tuner.apply(tbl, preds[0]) == tuple(cache[k])
     again = Autotuner(esc, str(tmp_path / "tune.json"))
     assert again.cache == tuner.cache
+
+
+def test_autotuned_batch_matches_oracle(tmp_path):
+    """A prepared batch whose launch shapes the tuner chose (its choices
+    applied per class) gives the oracle's counts, ordered ids and projected
+    values for every sub-query, replayed twice from its CUDA graph."""
+    import numpy as np
+    import oracle
+    from paper_1901_01488_gb300 import esc
+    from paper_1901_01488_gb300.autotune import Autotuner, DEFAULT
+    sizes = (50_000, 700_003, 3_000_000)
+    tabs = [datagen.skewed_table(n, seed=62 + i, device="cuda") for i, n in enumerate(sizes)]
+    etabs = [esc.Table.from_datagen(t) for t in tabs]
+    hosts = [t.host() for t in tabs]
+    work = datagen.batch_workload(36, seed=9, sizes=sizes)
+    proj = datagen.SKEWED_PROJECTION
+    preds = [esc.Predicate(etabs[ti], p.text, proj) for ti, p in work]
+    tuner = Autotuner(esc, str(tmp_path / "tune.json"), repeats=1)
+    for k, et in enumerate(etabs):
+        mine = [p for (ti, _), p in zip(work, preds) if ti == k]
+        tuner.tune(et, mine[0::2], materialise=True)
+        tuner.tune(et, mine[1::2], materialise=False)
+    applied = []
+    expect, rows = [], []
+    for j, ((ti, p), pr) in enumerate(zip(work, preds)):
+        mat = j % 2 == 0
+        applied.append(tuner.apply(etabs[ti], pr, materialise=mat))
+        ids, pv = oracle.select(p.text, hosts[ti], proj)
+        expect.append((ids, pv))
+        rows.append(pr.alloc_rows(len(ids) + 2) if mat else None)
+    assert any(a != DEFAULT for a in applied)           # the tuner's choices are really in use
+    b = esc.esc_batch_prepare([etabs[ti].handle for ti, _ in work], [p.handle for p in preds], rows)
+    dev_counts = torch.zeros(len(work), dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        for r in rows:
+            if r is not None:
+                r[1].fill_(-1)
+        dev_counts.zero_()
+        esc.esc_batch_run(b, dev_counts)
+        torch.cuda.synchronize()
+        counts = dev_counts.tolist()
+        for j, (ids, pv) in enumerate(expect):
+            assert counts[j] == len(ids), work[j][1].text
+            if rows[j] is not None:
+                got = rows[j][1][:len(ids)].cpu().numpy().view(np.uint32)
+                assert np.array_equal(got, ids), work[j][1].text
+                for name, c in zip(proj, rows[j][2]):
+                    assert np.array_equal(c[:len(ids)].cpu().numpy(), pv[name]), (work[j][1].text, name)
+    esc.esc_batch_destroy(b)

@@ -1,9 +1,10 @@
-"""Continuous batching: every served result equals the same sub-query run
-alone, and admission never exceeds the device-memory budget."""
+"""Continuous batching: every served result equals the oracle's and the same
+sub-query run alone, and admission never exceeds the device-memory budget."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1901_01488_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +42,19 @@ def test_served_results_equal_alone(esc):
     assert srv.shared_launches > 0          # same-table count requests shared a pass
     assert srv.peak_bytes <= 256 << 20 or max(serve.request_bytes(etabs[r.table].nrows, r, srv.widths[r.table])
                                                for r in reqs) > 256 << 20
+    hosts = [t.host() for t in tabs]
     for r in done:
+        # the oracle decides every served count and every materialised row list
+        if not r.proj:
+            assert r.count == oracle.count_parallel(r.text, hosts[r.table], 8), r.text
+        else:
+            ids, pv = oracle.select(r.text, hosts[r.table], tuple(r.proj))
+            n = len(ids)
+            assert r.count == n, r.text
+            assert np.array_equal(r.rows[1][:n].cpu().numpy().view(np.uint32), ids), r.text
+            for name, a in zip(r.proj, r.rows[2]):
+                assert np.array_equal(a[:n].cpu().numpy(), pv[name]), (r.text, name)
+        # and the same sub-query run alone through the library gives the same answer
         p = esc.Predicate(etabs[r.table], r.text, tuple(r.proj))
         if not r.proj:
             assert r.count == esc.count(etabs[r.table], p), r.text
