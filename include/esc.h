@@ -45,7 +45,8 @@ typedef enum esc_status {
     ESC_ETRUNC = 4,    /* output rows did not fit: count is exact, rows truncated */
     ESC_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
     ESC_EBUSY = 6,     /* resource in use */
-    ESC_ECUDA = 7      /* a CUDA runtime call failed */
+    ESC_ECUDA = 7,     /* a CUDA runtime call failed */
+    ESC_EBOUNDS = 8    /* checked build only: a kernel found an index out of range (and skipped the access) */
 } esc_status;
 
 /* Column element types.  Values are widened to int64 for every comparison:
@@ -323,6 +324,18 @@ esc_status esc_timestamp(uint64_t *dev_ns, void *stream);
  * outcome) and leaves the context usable.  Exercises failure detection
  * without faulting a GPU. */
 esc_status esc_selftest_wait_timeout(uint64_t limit_ns, void *stream);
+
+/* Test hooks (not in the paper; they exercise the error paths without a
+ * GPU fault).  esc_debug_fail_allocs(n): the library's next n device
+ * allocations (per-call scratch, batch memory) fail with ESC_ENOMEM as if
+ * the device were out of memory, and the calls that make them return
+ * ESC_ENOMEM having launched nothing; n = 0 turns the injection off.
+ * esc_build_checked(&flag): *flag = 1 in the checked build
+ * (libesc_checked.so), whose kernels test the indices they are about to use
+ * and report ESC_EBOUNDS (with the site and the index in the message)
+ * instead of touching memory out of range; 0 in the release build. */
+esc_status esc_debug_fail_allocs(int32_t n);
+esc_status esc_build_checked(int32_t *flag);
 
 #ifdef __cplusplus
 }

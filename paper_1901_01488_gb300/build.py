@@ -1,4 +1,8 @@
-"""Builds libesc.so in-tree for sm_103a (nvcc + the host C++ compiler).
+"""Builds libesc.so in-tree for sm_103a (nvcc + the host C++ compiler), and
+libesc_checked.so, the same sources compiled with -DESC_CHECKED: kernels
+that test every index they use and report ESC_EBOUNDS instead of touching
+memory out of range (the stand-in for a memory checker; tests load it with
+ESC_CHECKED=1 in the environment).
 
 Usage: python -m paper_1901_01488_gb300.build [--force]
 """
@@ -15,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libesc.so")
+LIB_CHECKED = os.path.join(HERE, "libesc_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["esc_scan.cu", "esc_semijoin.cu", "esc_mlp.cu"]
@@ -29,18 +34,19 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, verbose_ptxas: bool, checked: bool = False) -> str:
+    obj = os.path.join(OBJ, ("checked_" if checked else "") + os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if not _stale(obj, [path] + HEADERS):
         return obj
+    defs = ["-DESC_CHECKED"] if checked else []
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+        cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *defs,
                "-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
         if verbose_ptxas:
             cmd[1:1] = ["-Xptxas", "-v"]
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", "/usr/local/cuda/include",
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *defs, "-I", "/usr/local/cuda/include",
                "-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -68,15 +74,18 @@ def _build_locked(force: bool, verbose_ptxas: bool) -> str:
         for f in os.listdir(OBJ):
             if f.endswith(".o"):
                 os.remove(os.path.join(OBJ, f))
-    with ThreadPoolExecutor(len(CU) + len(CPP)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), CU + CPP))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+    jobs = [(s, False) for s in CU + CPP] + [(s, True) for s in CU + CPP]
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(lambda j: _compile(j[0], verbose_ptxas, j[1]), jobs))
+    n = len(CU) + len(CPP)
+    for lib, lib_objs in ((LIB, objs[:n]), (LIB_CHECKED, objs[n:])):
+        if force or _stale(lib, lib_objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *lib_objs]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+            os.replace(tmp, lib)
     return LIB
 
 

@@ -14,6 +14,7 @@
 //    with the child that needs the deepest stack first (Sethi-Ullman order),
 //    so the evaluation stack stays within 8 entries.
 #include <algorithm>
+#include <atomic>
 #include <cctype>
 #include <cinttypes>
 #include <cstdio>
@@ -793,6 +794,22 @@ void fill_query_program(const esc_pred *p, Query *q) {
   for (size_t i = 0; i < p->pool.size(); ++i) q->pool[i] = p->pool[i];
 }
 
+std::atomic<int32_t> g_fail_allocs{0};
+
+bool inject_alloc_failure() {
+  int32_t n = g_fail_allocs.load();
+  while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+  }
+  return n > 0;
+}
+
+esc_status device_status(const ScratchHdr &h, const char *where) {
+  if (h.status == (unsigned)ESC_EBOUNDS)
+    return fail(ESC_EBOUNDS, std::string(where) + ": checked build: an index out of range at site " +
+                                 std::to_string(h.site) + " (" + std::to_string(h.value) + "), access skipped");
+  return fail((esc_status)h.status, std::string(where) + ": a bounded device-side wait gave up");
+}
+
 }  // namespace esc
 
 using namespace esc;
@@ -812,8 +829,26 @@ const char *esc_status_string(esc_status s) {
     case ESC_ETIMEOUT: return "ESC_ETIMEOUT";
     case ESC_EBUSY: return "ESC_EBUSY";
     case ESC_ECUDA: return "ESC_ECUDA";
+    case ESC_EBOUNDS: return "ESC_EBOUNDS";
   }
   return "ESC_UNKNOWN";
+}
+
+esc_status esc_debug_fail_allocs(int32_t n) {
+  if (n < 0) return fail(ESC_EINVAL, "esc_debug_fail_allocs: n must be >= 0");
+  g_fail_allocs.store(n);
+  clear_error();
+  return ESC_OK;
+}
+
+esc_status esc_build_checked(int32_t *flag) {
+  if (!flag) return fail(ESC_EINVAL, "esc_build_checked: flag is NULL");
+#ifdef ESC_CHECKED
+  *flag = 1;
+#else
+  *flag = 0;
+#endif
+  return ESC_OK;
 }
 
 esc_status esc_udf_magic(uint64_t d, uint64_t *mult, int32_t *sh1, int32_t *sh2) {

@@ -114,8 +114,34 @@ struct ScratchHdr {
   unsigned int ticket;   // next global tile ticket
   unsigned int status;   // esc_status raised on the device (0 = OK)
   unsigned int abort;    // set together with status; everyone stops working
-  unsigned int pad;
+  unsigned int site;     // checked build: where the first out-of-range index was found
+  unsigned long long value;  // checked build: that index
+  unsigned long long pad;
 };
+static_assert(sizeof(ScratchHdr) == 32, "ScratchHdr layout");
+
+#ifdef __CUDACC__
+// Checked build (-DESC_CHECKED, libesc_checked.so; the stand-in for a memory
+// checker): ESC_INB(hdr, cond, site, value) is false when an index a kernel
+// is about to use is out of range.  The first such event of a launch records
+// ESC_EBOUNDS, the site number and the index in the launch header and makes
+// the launch wind down; the access itself is skipped.  In the release build
+// every check is `true` and compiles away.
+#ifdef ESC_CHECKED
+__device__ __forceinline__ bool inb(bool ok, ScratchHdr *hdr, uint32_t site, uint64_t value) {
+  if (!ok && atomicCAS(&hdr->status, 0u, (unsigned)ESC_EBOUNDS) == 0u) {
+    hdr->site = site;
+    hdr->value = value;
+    __threadfence();
+    atomicExch(&hdr->abort, 1u);
+  }
+  return ok;
+}
+#define ESC_INB(hdr, cond, site, value) esc::inb((cond), (hdr), (site), (uint64_t)(value))
+#else
+#define ESC_INB(hdr, cond, site, value) true
+#endif
+#endif
 
 }  // namespace esc
 
@@ -144,6 +170,12 @@ namespace esc {
 int dtype_width(int32_t dt);
 esc_status fail(esc_status s, const std::string &msg);
 void clear_error();
+// The status a launch's header reports, as an error with its message
+// (ESC_EBOUNDS: the site and the index the checked build recorded).
+esc_status device_status(const ScratchHdr &h, const char *where);
+// Test hook: true when a device allocation of the library is to fail
+// (esc_debug_fail_allocs counts them down).
+bool inject_alloc_failure();
 // Defaults of esc_tuning.
 constexpr esc_tuning kDefaultTuning{32768u, 512u, 8, 0};
 // Fills the static part of a Query (program, read columns, projection) for a pred.

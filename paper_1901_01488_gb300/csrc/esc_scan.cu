@@ -558,6 +558,42 @@ struct SmemLayout {
   static constexpr size_t total = res + kStages * kResBytes;
 };
 
+// Checked build: everything the evaluation of a stage will index -- every
+// operand slice of the staged tile, the constant pool entries of IN lists,
+// sets and udf moduli, jump targets, the groups' result bytes -- lies inside
+// its buffer (warp-collective; lanes take instructions).  True in the
+// release build.
+__device__ __forceinline__ bool stage_in_bounds(const Query *Q, int ngroups, ScratchHdr *hdr, int lane) {
+#ifdef ESC_CHECKED
+  bool ok = ESC_INB(hdr, ngroups >= 0 && (uint32_t)ngroups <= Q->gmax && Q->gmax <= (uint32_t)kResGroups, 10, ngroups);
+  ok = ok && ESC_INB(hdr, Q->ninstr >= 0 && Q->ninstr <= kMaxInstr && Q->nref <= kMaxRef, 11, Q->ninstr);
+  const uint64_t span = (uint64_t)ngroups * kGroup;
+  for (int pc = lane; ok && pc < Q->ninstr; pc += 32) {
+    const Instr &I = Q->code[pc];
+    const bool opd = I.op == OP_RANGE || I.op == OP_IN || I.op == OP_INSET || I.op == OP_UDF;
+    if (opd) {
+      ok = ok && ESC_INB(hdr, I.ref < Q->nref, 12, pc);
+      ok = ok && ESC_INB(hdr, I.soff + span * width_of(I.dtype) <= kStageBytes, 13, pc);
+    }
+    if (I.op == OP_UDF) {
+      ok = ok && ESC_INB(hdr, I.ref2 < Q->nref, 12, pc);
+      ok = ok && ESC_INB(hdr, I.soff2 + span * width_of(I.dtype2) <= kStageBytes, 13, pc);
+      ok = ok && ESC_INB(hdr, I.off + 6u <= (uint32_t)kMaxPool, 14, pc);
+    }
+    if (I.op == OP_IN) ok = ok && ESC_INB(hdr, (uint32_t)I.off + I.n <= (uint32_t)kMaxPool, 14, pc);
+    if (I.op == OP_INSET) ok = ok && ESC_INB(hdr, I.off + 4u <= (uint32_t)kMaxPool, 14, pc);
+    if (I.op == OP_JZ || I.op == OP_JNZ) ok = ok && ESC_INB(hdr, I.off <= (uint32_t)Q->ninstr, 15, pc);
+  }
+  return __all_sync(FULL, ok);
+#else
+  (void)Q;
+  (void)ngroups;
+  (void)hdr;
+  (void)lane;
+  return true;
+#endif
+}
+
 // ------------------------------------------------------------------ the scan kernel
 // Warp 0: producer (unit tickets, bulk copies).  Warps 1..: consumers
 // (evaluate; count; compaction: bitmap words and unit totals; bitmap mode:
@@ -653,6 +689,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           tail = bytes - bulk;
           src = Q->ref_ptr[lane] + (size_t)r0 * w;
           dst = stage + Q->stage_off[lane];
+          // checked build: the copy stays inside the stage and the column
+          if (!ESC_INB(hdr, Q->stage_off[lane] + bytes <= kStageBytes, 1, Q->stage_off[lane] + bytes) ||
+              !ESC_INB(hdr, (uint64_t)r0 + rows <= Q->nrows, 2, r0 + rows))
+            bulk = tail = 0;
         }
         if (__ballot_sync(FULL, tail != 0)) {
           for (int c = 0; c < nref; ++c) {
@@ -734,7 +774,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       if (lane == 0) j = (int)atomicAdd(&take[s], 1u);
       return __shfl_sync(FULL, j, 0);
     };
-    if (mt.dead == 0) {
+    if (mt.dead == 0 && stage_in_bounds(Q, ngroups, hdr, lane)) {
       // one evaluation loop for every mode (a single inlined copy of the
       // interpreter); the per-group epilogue branches on the mode (uniform)
       const uint32_t nwords = (Q->nrows + 31u) / 32u;
@@ -756,7 +796,9 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           if (mode == MODE_SELECT) {
             // the group's compaction unit (kMaxUnitGroups groups): flush the
             // running total when it changes (warp-uniform)
-            unsigned long long *up = Q->unit_total + (mt.tile * Q->gmax + (uint32_t)gs[i]) / (uint32_t)kMaxUnitGroups;
+            const uint32_t wu = (mt.tile * Q->gmax + (uint32_t)gs[i]) / (uint32_t)kMaxUnitGroups;
+            if (!ESC_INB(hdr, wu < Q->nwunits, 16, wu)) continue;
+            unsigned long long *up = Q->unit_total + wu;
             if (up != uacc_ptr) {
               if (uacc_ptr) {
                 const uint32_t t = __reduce_add_sync(FULL, uacc);
@@ -801,7 +843,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           resdone[s] = 0;
           const uint32_t ng = (uint32_t)ngroups;
           const uint32_t *rb = reinterpret_cast<const uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
-          bulk_store(Q->bitmap + (size_t)mt.tile * Q->gmax * 8u, rb, ng * 32u);
+          if (ESC_INB(hdr, ((uint64_t)mt.tile * Q->gmax + ng) <= (uint64_t)Q->ntiles * Q->gmax, 17, mt.tile))
+            bulk_store(Q->bitmap + (size_t)mt.tile * Q->gmax * 8u, rb, ng * 32u);
           bulk_commit_wait_read();
         }
         __syncwarp();
@@ -909,7 +952,7 @@ struct GatherInfo {
 // slot relative to the warp's first group) to the outputs: 4 entries per
 // lane, each column's loads issued before its stores.
 __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t *ent, uint32_t n, uint32_t row_ref,
-                                             unsigned long long pos_ref, int lane) {
+                                             unsigned long long pos_ref, int lane, ScratchHdr *hdr) {
   const uint64_t cap = G.capacity;
   for (uint32_t t0 = 0; t0 < n; t0 += 128) {
     uint32_t row[4];
@@ -924,7 +967,7 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
         const uint32_t e = ent[t];
         row[k] = row_ref + (e >> 16);
         pos[k] = pos_ref + (e & 0xffffu);
-        if (pos[k] < cap) ok |= 1u << k;
+        if (pos[k] < cap && ESC_INB(hdr, row[k] < G.nrows, 22, row[k])) ok |= 1u << k;
       }
     }
 #pragma unroll
@@ -950,7 +993,7 @@ __device__ __forceinline__ void flush_sparse(const GatherInfo &G, const uint32_t
 // time; a column wider than that is read in place); each output slot then
 // takes its row's value from shared memory, so that the stores coalesce.
 __device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &W, int j, uint32_t g, uint32_t cnt,
-                                            unsigned long long base, int lane) {
+                                            unsigned long long base, int lane, ScratchHdr *hdr) {
   const uint64_t cap = G.capacity;
   // rows 8l .. 8l+7 of the group: bits 2(l/8), 2(l/8)+1 of bytes 4(l%8) ..
   // 4(l%8)+3 (word l%8 of the lane-major bitmap), packed in row order
@@ -967,7 +1010,7 @@ __device__ __forceinline__ void dense_group(const GatherInfo &G, WriteWarpSmem &
   uint32_t r = incl - cl;
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if ((bits8 >> k) & 1u) W.sids[r++] = 8u * (uint32_t)lane + (uint32_t)k;
+    if (((bits8 >> k) & 1u) && ESC_INB(hdr, r < (uint32_t)kGroup, 24, r)) W.sids[r++] = 8u * (uint32_t)lane + (uint32_t)k;
   const uint32_t grow = g * kGroup;
   const int np = G.nproj;
   int c0 = 0;
@@ -1059,6 +1102,7 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     }
   }
   const uint32_t u = blockIdx.x - Q->wunit_base;
+  if (!ESC_INB(L.hdr, u < Q->nwunits, 20, u)) return;  // uniform: the whole block
   const uint32_t urows = kMaxUnitRows;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
@@ -1076,7 +1120,7 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   unsigned long long *st = Q->unit_status;
   const unsigned long long utot = __ldcg(&tot[u]);
   uint4 wlo = make_uint4(0, 0, 0, 0), whi = wlo;
-  if (valid) {
+  if (valid && ESC_INB(L.hdr, grp_l < (uint64_t)Q->ntiles * Q->gmax, 21, grp_l)) {
     const uint4 *bw = reinterpret_cast<const uint4 *>(Q->bitmap + (size_t)grp_l * 8);
     wlo = __ldcg(bw);
     whi = __ldcg(bw + 1);
@@ -1156,7 +1200,8 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
     for (uint32_t dm = dm0; dm; dm &= dm - 1) {
       const int j = __ffs(dm) - 1;
       const unsigned long long base = __shfl_sync(FULL, base_l, j);
-      if (base < G.capacity) dense_group(G, W, j, __shfl_sync(FULL, grp_l, j), __shfl_sync(FULL, c, j), base, lane);
+      if (base < G.capacity)
+        dense_group(G, W, j, __shfl_sync(FULL, grp_l, j), __shfl_sync(FULL, c, j), base, lane, L.hdr);
     }
     // the other groups: lane = group, entries staged in slot order
     const uint32_t sc = dense_l ? 0u : c;
@@ -1191,13 +1236,14 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
               for (uint32_t xm = wv & (0x03030303u << (2 * jb)); xm != 0u && e < eend; xm &= xm - 1u, ++e) {
                 const uint32_t bpos = (uint32_t)__ffs(xm) - 1u;  // 8 * byte + 2j + i
                 const uint32_t rr = 64u * jb + 2u * (4u * wi + (bpos >> 3)) + ((bpos & 7u) - 2u * jb);
-                if (e >= win) ent[e - win] = ((rrel + rr) << 16) | (srel + e - sx);
+                if (e >= win && ESC_INB(L.hdr, e - win < kStageEntries, 23, e - win))
+                  ent[e - win] = ((rrel + rr) << 16) | (srel + e - sx);
               }
             }
           }
         }
         __syncwarp();
-        flush_sparse(G, ent, min(stot - win, kStageEntries), row_ref, pos_ref, lane);
+        flush_sparse(G, ent, min(stot - win, kStageEntries), row_ref, pos_ref, lane, L.hdr);
         __syncwarp();
       }
     }
@@ -1629,6 +1675,7 @@ esc_status alloc_async(void **p, size_t bytes, cudaStream_t st) {
   DeviceState *d;
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
+  if (inject_alloc_failure()) return fail(ESC_ENOMEM, "device scratch allocation: injected failure (esc_debug_fail_allocs)");
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes, d->pool, st);
   if (e != cudaSuccess) return fail(ESC_ENOMEM, std::string("device scratch allocation: ") + cudaGetErrorString(e));
   return ESC_OK;
@@ -1764,7 +1811,7 @@ esc_status finish_single(SingleScratch *sc, uint64_t *count, cudaStream_t st) {
     cudaError_t e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
     return fail(ESC_ECUDA, std::string("sub-query readback: ") + cudaGetErrorString(e));
   }
-  if (h.hdr.status != 0) return fail((esc_status)h.hdr.status, "a bounded device-side wait gave up");
+  if (h.hdr.status != 0) return device_status(h.hdr, "sub-query");
   if (count) *count = h.count;
   return ESC_OK;
 }
@@ -1897,7 +1944,7 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
   b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + (size_t)zeroed;
   const size_t total = q_span + b->scratch_bytes + left_bytes + (size_t)other;
-  cudaError_t e = cudaMalloc(&b->dev_mem, total);
+  cudaError_t e = inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&b->dev_mem, total);
   if (e != cudaSuccess) {
     batch_free(b);
     return fail(ESC_ENOMEM, std::string("esc_batch_prepare: cudaMalloc: ") + cudaGetErrorString(e));
@@ -2011,7 +2058,7 @@ esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred 
   }
   batch_free(b);
   if (s != ESC_OK) return s;
-  if (h.status != 0) return fail((esc_status)h.status, "a bounded device-side wait gave up");
+  if (h.status != 0) return device_status(h, "esc_selectivity_batch");
   bool trunc = false;
   if (rows)
     for (int i = 0; i < n; ++i) {
@@ -2365,7 +2412,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
   NoAllocHead back;
   ESC_CK(cudaMemcpyAsync(&back, h, sizeof back, cudaMemcpyDeviceToHost, st));
   ESC_CK(cudaStreamSynchronize(st));
-  if (back.hdr.status != 0) return fail((esc_status)back.hdr.status, "a bounded device-side wait gave up");
+  if (back.hdr.status != 0) return device_status(back.hdr, "esc_selectivity_noalloc");
   *count = back.count;
   if (rows) {
     rows->written = std::min<uint64_t>(back.count, rows->capacity);

@@ -40,6 +40,8 @@ struct SjParams {
   int32_t ndims;
   uint32_t nrows;
   unsigned long long *hist;            // 16 bins, zeroed
+  ScratchHdr *hdr;                     // launch header (zeroed): the checked build's findings
+  uint32_t smem_words;                 // shared-memory words the launch has (checked build)
 };
 
 __device__ __forceinline__ int4 ld_stream(const int32_t *p) {
@@ -60,6 +62,15 @@ __device__ __forceinline__ uint32_t test_bit(const uint32_t *bm, uint32_t key, u
   if (shared) return (bm[min(key >> 5, wlast)] >> (key & 31u)) & 1u;
   const uint32_t w = __ldg(&bm[min(key >> 5, wlast)]);
   return key < rows ? (w >> (key & 31u)) & 1u : 0u;
+}
+
+// The same, in the checked build: the word index is tested against the
+// bitmap's words (in shared memory: its copy and the zero word).
+__device__ __forceinline__ uint32_t test_bit_checked(const uint32_t *bm, uint32_t key, uint32_t rows, uint32_t wlast,
+                                                     bool shared, uint32_t words, ScratchHdr *hdr) {
+  const uint32_t wi = min(key >> 5, wlast);
+  if (!ESC_INB(hdr, wi < (shared ? words + 1 : words), 32, wi)) return 0u;
+  return test_bit(bm, key, rows, wlast, shared);
 }
 
 __device__ __forceinline__ void bump(uint64_t &lo, uint64_t &hi, uint32_t m) {
@@ -86,7 +97,13 @@ __device__ __forceinline__ uint32_t probe_row(const SjParams &P, const uint32_t 
                                               const uint32_t (&wmax)[ND], const int32_t (&k)[ND]) {
   uint32_t m = 0;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) m |= test_bit(bm[d], (uint32_t)k[d], P.dim_rows[d], wmax[d], d < NS) << d;
+  for (int d = 0; d < ND; ++d) {
+#ifdef ESC_CHECKED
+    m |= test_bit_checked(bm[d], (uint32_t)k[d], P.dim_rows[d], wmax[d], d < NS, P.words[d], P.hdr) << d;
+#else
+    m |= test_bit(bm[d], (uint32_t)k[d], P.dim_rows[d], wmax[d], d < NS) << d;
+#endif
+  }
   return m;
 }
 
@@ -101,7 +118,7 @@ __global__ void __launch_bounds__(kSjThreads, 2) semijoin_kernel(const __grid_co
     for (uint32_t w = threadIdx.x; w <= P.words[d]; w += blockDim.x) {
       uint32_t x = w < P.words[d] ? P.bitmap[d][w] : 0u;
       if (w + 1 == P.words[d] && tail) x &= (1u << tail) - 1u;
-      sbm[P.smem_off[d] + w] = x;
+      if (ESC_INB(P.hdr, P.smem_off[d] + w < P.smem_words, 31, P.smem_off[d] + w)) sbm[P.smem_off[d] + w] = x;
     }
   }
   if (threadIdx.x < 16) bins[threadIdx.x] = 0;
@@ -121,7 +138,7 @@ __global__ void __launch_bounds__(kSjThreads, 2) semijoin_kernel(const __grid_co
   // warp-uniform trip count (the flush is warp-collective); lanes past the end idle
   for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < nchunks; wb += stride) {
     const uint32_t ch = wb + (threadIdx.x & 31u);
-    if (ch < nchunks) {
+    if (ch < nchunks && ESC_INB(P.hdr, (uint64_t)ch * 8 + 8 <= P.nrows, 30, ch)) {
     int4 v[ND][2];
 #pragma unroll
     for (int d = 0; d < ND; ++d)
@@ -249,14 +266,17 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void *mem = nullptr;
-  // the library's device pool (memory stays reserved between calls)
-  if (esc_status as = alloc_async(&mem, 16 * 8, st); as != ESC_OK) return as;
-  cudaError_t e = cudaMemsetAsync(mem, 0, 16 * 8, st);
+  // the library's device pool (memory stays reserved between calls): 16
+  // bins, then the launch header
+  if (esc_status as = alloc_async(&mem, 16 * 8 + sizeof(ScratchHdr), st); as != ESC_OK) return as;
+  cudaError_t e = cudaMemsetAsync(mem, 0, 16 * 8 + sizeof(ScratchHdr), st);
   P.hist = static_cast<unsigned long long *>(mem);
+  P.hdr = reinterpret_cast<ScratchHdr *>(static_cast<uint8_t *>(mem) + 16 * 8);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = (size_t)std::max<uint32_t>(smem_words, 4) * 4;
+  P.smem_words = (uint32_t)(smem / 4);
   const uint32_t chunks = P.nrows / 8u;
   const int grid = std::max(1, std::min<int>(sms * 2, (int)((chunks + kSjThreads - 1) / kSjThreads)));
   if (e == cudaSuccess) {
@@ -267,11 +287,16 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
       default: e = launch_nd<4>(P, ns, smem, grid, st); break;
     }
   }
-  unsigned long long h[16];
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, mem, sizeof h, cudaMemcpyDeviceToHost, st);
+  struct {
+    unsigned long long h[16];
+    ScratchHdr hdr;
+  } back;
+  unsigned long long *h = back.h;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&back, mem, sizeof back, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(mem, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(ESC_ECUDA, std::string("esc_semijoin_counts: ") + cudaGetErrorString(e));
+  if (back.hdr.status != 0) return device_status(back.hdr, "esc_semijoin_counts");
   // bins are in probe order (bit i = dimension order[i]): back to the caller's bits
   const uint32_t nsub = 1u << ndims;
   uint64_t hc[16] = {0};

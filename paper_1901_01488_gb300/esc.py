@@ -17,13 +17,16 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libesc.so")
+# ESC_CHECKED=1 loads the checked build (kernels that test every index they
+# use and report ESC_EBOUNDS); the release build otherwise
+LIB_PATH = os.path.join(_HERE, "libesc_checked.so" if os.environ.get("ESC_CHECKED") == "1" else "libesc.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libesc.so is not built ({LIB_PATH}); run `python -m paper_1901_01488_gb300.build`")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); "
+                      "run `python -m paper_1901_01488_gb300.build`")
 _lib = ctypes.CDLL(LIB_PATH)
 
-ESC_OK, ESC_EINVAL, ESC_ETYPE, ESC_ENOMEM, ESC_ETRUNC, ESC_ETIMEOUT, ESC_EBUSY, ESC_ECUDA = range(8)
+ESC_OK, ESC_EINVAL, ESC_ETYPE, ESC_ENOMEM, ESC_ETRUNC, ESC_ETIMEOUT, ESC_EBUSY, ESC_ECUDA, ESC_EBOUNDS = range(9)
 DTYPE_CODE = {"i32": 0, "i64": 1, "u8": 2, "u16": 3}
 WIDTH = {"i32": 4, "i64": 8, "u8": 1, "u16": 2}
 TORCH_DTYPE = {"i32": torch.int32, "i64": torch.int64, "u8": torch.uint8, "u16": torch.int16}
@@ -79,6 +82,8 @@ _sig = {
     "esc_selectivity_shared_async": ([_P, ctypes.POINTER(_P), ctypes.c_int32, _P, _P], _S),
     "esc_selectivity_batch_async": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32,
                                      ctypes.POINTER(esc_rows), _P, _P, _P], _S),
+    "esc_debug_fail_allocs": ([ctypes.c_int32], _S),
+    "esc_build_checked": ([ctypes.POINTER(ctypes.c_int32)], _S),
     "esc_mlp_forward": ([_P, ctypes.c_uint64, _P, _P, _P, _P], _S),
     "esc_mlp_grad": ([_P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P], _S),
     "esc_mlp_adam": ([_P, _P, _P, _P, _P, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -347,6 +352,16 @@ def esc_mlp_adam(params: torch.Tensor, w_bf16: torch.Tensor, grad: torch.Tensor,
                  stream=None) -> None:
     _check(_lib.esc_mlp_adam(params.data_ptr(), w_bf16.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(),
                              params.numel(), lr, beta1, beta2, eps, step, _stream(stream)), "esc_mlp_adam")
+
+
+def esc_debug_fail_allocs(n: int) -> None:
+    _check(_lib.esc_debug_fail_allocs(n), "esc_debug_fail_allocs")
+
+
+def esc_build_checked() -> bool:
+    flag = ctypes.c_int32(0)
+    _check(_lib.esc_build_checked(ctypes.byref(flag)), "esc_build_checked")
+    return bool(flag.value)
 
 
 def esc_last_error() -> str:

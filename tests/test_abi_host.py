@@ -268,3 +268,17 @@ def test_headline_predicates_read_columns(esc):
     for p in datagen.skewed_predicates(200):
         listing = esc.Predicate(tbl, p.text, datagen.SKEWED_PROJECTION).explain()
         assert any(l.startswith("ref ") for l in listing.splitlines()), p.text
+
+
+def test_checked_build_loads_and_says_so(esc):
+    """The checked build (kernels that test their indices) exports the same
+    symbols and reports itself as checked; the release build does not."""
+    import subprocess
+    import sys
+    assert esc.esc_build_checked() is False
+    code = ("import sys; sys.path.insert(0, sys.argv[1]); from paper_1901_01488_gb300 import esc; "
+            "assert esc.LIB_PATH.endswith('libesc_checked.so'); assert esc.esc_build_checked() is True; "
+            "[getattr(esc._lib, n) for n in esc.EXPORTED]; print('ok')")
+    env = dict(os.environ, ESC_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
