@@ -212,6 +212,19 @@ esc_status esc_selectivity_noalloc(const esc_table *table, const esc_pred *pred,
  * different streams are not allowed (ESC_EBUSY is not detected). */
 esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *const *preds,
                              int32_t n, const esc_rows *rows, esc_batch **out);
+
+/* Same as esc_batch_prepare, in `waves` launches (1..16) instead of one, for
+ * per-sub-query latency: the sub-queries are ordered by the bytes their
+ * scans read, smallest first (esc_batch_prepare orders them the same way),
+ * and cut into consecutive waves whose work doubles from one to the next
+ * (the last about half of the batch).  Each wave is one persistent scan
+ * launch and, when it materialises, one write launch, all captured in the
+ * batch's CUDA graph; a sub-query completes with its wave, so small ones
+ * complete early.  Results, completion times and status as for
+ * esc_batch_prepare.  Not in the paper (the optimizer's sub-queries are
+ * issued one per table with a selection, Sec. 2). */
+esc_status esc_batch_prepare_waves(const esc_table *const *tables, const esc_pred *const *preds,
+                                   int32_t n, const esc_rows *rows, int32_t waves, esc_batch **out);
 esc_status esc_batch_run(esc_batch *batch, uint64_t *dev_counts, uint64_t *dev_done_ns,
                          void *stream);
 esc_status esc_batch_destroy(esc_batch *batch);

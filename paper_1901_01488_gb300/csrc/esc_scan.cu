@@ -1871,9 +1871,8 @@ esc_status esc_bitmap_build(const esc_table *dim, const esc_pred *p, uint32_t *d
 
 struct esc_batch {
   int32_t n = 0;
+  int32_t nwaves = 1;               // scan (+ write) launches, one header each at the start of scratch
   int device = 0;
-  uint32_t total_units = 0;
-  uint32_t write_blocks = 0;
   void *dev_mem = nullptr;          // queries + scratch, owned
   Query *queries = nullptr;         // device
   uint8_t *scratch = nullptr;       // device: hdr, counts, done, countdowns, unit words
@@ -1896,50 +1895,97 @@ void batch_free(esc_batch *b) {
   delete b;
 }
 
-}  // namespace
+constexpr int kMaxWaves = 16;
 
-extern "C" {
+// Work of a sub-query, for ordering a batch and grouping it into waves: the
+// bytes its scan reads (0 for a program folded to a constant).
+uint64_t query_work(const Query &q) {
+  if (q.is_const) return 0;
+  uint64_t bpr = 0;
+  for (int i = 0; i < q.nref; ++i) bpr += q.ref_w[i];
+  return (uint64_t)q.nrows * std::max<uint64_t>(bpr, 1);
+}
 
-esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
-                             const esc_rows *rows, esc_batch **out) {
+// A prepared batch: the sub-queries sorted by work (smallest first) and cut
+// into `waves` consecutive groups whose work doubles from one to the next
+// (the last holds about half of it); each wave is one persistent scan launch
+// and, when it materialises, one write launch.  Counts, completion times and
+// countdowns stay indexed in the caller's order.
+esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
+                         const esc_rows *rows, int32_t waves, esc_batch **out) {
   if (!out) return fail(ESC_EINVAL, "esc_batch_prepare: out is NULL");
   *out = nullptr;
   if (n < 1 || !tables || !preds) return fail(ESC_EINVAL, "esc_batch_prepare: need n >= 1 tables and predicates");
+  if (waves < 1 || waves > kMaxWaves) return fail(ESC_EINVAL, "esc_batch_prepare: waves must be 1..16");
   DeviceState *d;
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
-  std::vector<Query> qs((size_t)n);
-  std::vector<uint32_t> cidx;
-  uint64_t units = 0, wunits = 0, zeroed = 0, other = 0;
+  std::vector<Query> qin((size_t)n);
   for (int i = 0; i < n; ++i) {
     const esc_rows *r = rows ? &rows[i] : nullptr;
     const bool compact = r && (r->capacity > 0 || r->row_ids != nullptr);
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
-                           &qs[i])) != ESC_OK)
+                           &qin[i])) != ESC_OK)
       return s;
-    mark_constant(qs[i]);
-    if (qs[i].is_const) cidx.push_back((uint32_t)i);
-    qs[i].unit_base = (uint32_t)units;
-    qs[i].wunit_base = (uint32_t)wunits;
-    units += qs[i].nunits;
-    if (compact) {
-      wunits += qs[i].nwunits;
-      zeroed += select_zeroed_bytes(qs[i]);
-      other += select_other_bytes(qs[i]);
+    mark_constant(qin[i]);
+  }
+  // smallest work first (stable: equal work keeps the caller's order)
+  std::vector<int> ord((size_t)n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return query_work(qin[a]) < query_work(qin[b]); });
+  std::vector<Query> qs((size_t)n);
+  uint64_t total_work = 0;
+  for (int k = 0; k < n; ++k) {
+    qs[k] = qin[ord[k]];
+    total_work += query_work(qs[k]);
+  }
+  // wave k ends once the work so far reaches total / 2^(waves-1-k)
+  std::vector<int> wend;
+  {
+    uint64_t acc = 0;
+    int k = 0;
+    for (int w = 0; w < waves; ++w) {
+      const uint64_t target = w + 1 == waves ? ~0ull : total_work >> (waves - 1 - w);
+      while (k < n && (acc < target || w + 1 == waves)) acc += query_work(qs[k++]);
+      if (k > (wend.empty() ? 0 : wend.back())) wend.push_back(k);
     }
-    if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
+    if (wend.empty() || wend.back() != n) wend.push_back(n);
+  }
+  const int nw = (int)wend.size();
+  std::vector<uint32_t> cidx;
+  std::vector<uint32_t> w_units((size_t)nw, 0), w_wunits((size_t)nw, 0);
+  std::vector<bool> w_udf((size_t)nw, false);
+  uint64_t zeroed = 0, other = 0;
+  for (int w = 0, k0 = 0; w < nw; k0 = wend[w++]) {
+    uint64_t units = 0, wunits = 0;
+    for (int k = k0; k < wend[w]; ++k) {
+      Query &q = qs[k];
+      if (q.is_const) cidx.push_back((uint32_t)k);
+      q.unit_base = (uint32_t)units;
+      q.wunit_base = (uint32_t)wunits;
+      units += q.nunits;
+      if (q.mode == MODE_SELECT) {
+        wunits += q.nwunits;
+        zeroed += select_zeroed_bytes(q);
+        other += select_other_bytes(q);
+      }
+      if (!q.is_const && program_has_udf(q)) w_udf[w] = true;
+      if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
+    }
+    w_units[w] = (uint32_t)units;
+    w_wunits[w] = (uint32_t)wunits;
   }
   esc_batch *b = new (std::nothrow) esc_batch;
   if (!b) return fail(ESC_ENOMEM, "esc_batch_prepare: out of host memory");
   b->n = n;
+  b->nwaves = nw;
   cudaGetDevice(&b->device);
-  b->total_units = (uint32_t)units;
-  b->write_blocks = (uint32_t)wunits;
-  // device memory: queries | zeroed every run: header, counts, done times,
-  // countdowns, unit totals + look-back words | countdown initial values |
-  // selection bitmaps
-  const size_t q_span = (sizeof(Query) * (size_t)n + 4 * (size_t)n + 255) & ~(size_t)255;  // queries + cidx
-  const size_t hdr_bytes = 256;
+  // device memory: queries (sorted) + constant indices | zeroed every run:
+  // one header per wave, counts, done times, countdowns (caller's order),
+  // unit totals + look-back words | countdown initial values | selection
+  // bitmaps
+  const size_t q_span = (sizeof(Query) * (size_t)n + 4 * (size_t)n + 255) & ~(size_t)255;
+  const size_t hdr_bytes = 256 * (size_t)nw;
   const size_t cnt_bytes = ((size_t)n * 8 + 255) & ~(size_t)255;
   const size_t left_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
   b->scratch_bytes = hdr_bytes + 2 * cnt_bytes + left_bytes + (size_t)zeroed;
@@ -1959,21 +2005,23 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   b->tiles_init = reinterpret_cast<unsigned int *>(b->scratch + b->scratch_bytes);
   uint8_t *op = b->scratch + b->scratch_bytes + left_bytes;
   std::vector<unsigned int> init((size_t)n);
-  bool udf = false;
-  for (int i = 0; i < n; ++i) udf = udf || (!qs[i].is_const && program_has_udf(qs[i]));
-  for (int i = 0; i < n; ++i) {
-    qs[i].count = &b->counts[i];
-    qs[i].done_ns = &b->done[i];
-    qs[i].tiles_left = &b->tiles_left[i];
-    if (qs[i].is_const) {
+  for (int k = 0; k < n; ++k) {
+    Query &q = qs[k];
+    const int i = ord[k];
+    int w = 0;
+    while (k >= wend[w]) ++w;
+    q.count = &b->counts[i];
+    q.done_ns = &b->done[i];
+    q.tiles_left = &b->tiles_left[i];
+    if (q.is_const) {
       init[i] = kConstBlocks;                         // counted down by the constant kernel
-    } else if (qs[i].mode == MODE_SELECT) {
-      select_bind(qs[i], zp, op);
-      zp += select_zeroed_bytes(qs[i]);
-      op += select_other_bytes(qs[i]);
-      init[i] = qs[i].nwunits;                        // counted down by the write kernel
+    } else if (q.mode == MODE_SELECT) {
+      select_bind(q, zp, op);
+      zp += select_zeroed_bytes(q);
+      op += select_other_bytes(q);
+      init[i] = q.nwunits;                            // counted down by the write kernel
     } else {
-      init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);  // counted down by the scan kernel
+      init[i] = q.ntiles * (unsigned)scan_consumers(w_udf[w]);  // counted down by the scan kernel
     }
   }
   if ((uintptr_t)op > (uintptr_t)base + total) {
@@ -1989,27 +2037,30 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
     batch_free(b);
     return fail(ESC_ECUDA, std::string("esc_batch_prepare: cudaMemcpy: ") + cudaGetErrorString(e));
   }
-  // Capture reset + scan + write into a graph once; runs replay it.
+  // Capture reset + constant kernel + (scan + write) per wave into a graph
+  // once; runs replay it.
   cudaStream_t cs;
   e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     batch_free(b);
     return fail(ESC_ECUDA, std::string("esc_batch_prepare: cudaStreamCreate: ") + cudaGetErrorString(e));
   }
-  Launch L;
-  std::memset(&L, 0, sizeof L);
-  L.queries = b->queries;
-  L.nq = n;
-  L.total_units = b->total_units;
-  L.hdr = reinterpret_cast<ScratchHdr *>(b->scratch);
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   esc_status ls = ESC_OK;
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->scratch, 0, b->scratch_bytes, cs);
     cudaMemcpyAsync(b->tiles_left, b->tiles_init, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
     if (!cidx.empty()) ls = launch_const_batch(b->queries, dev_cidx, (uint32_t)cidx.size(), cs);
-    if (ls == ESC_OK) ls = launch_scan(L, udf, cs);
-    if (ls == ESC_OK) ls = launch_write(L, b->write_blocks, cs);
+    for (int w = 0, k0 = 0; w < nw && ls == ESC_OK; k0 = wend[w++]) {
+      Launch L;
+      std::memset(&L, 0, sizeof L);
+      L.queries = b->queries + k0;
+      L.nq = wend[w] - k0;
+      L.total_units = w_units[w];
+      L.hdr = reinterpret_cast<ScratchHdr *>(b->scratch + 256 * (size_t)w);
+      ls = launch_scan(L, w_udf[w], cs);
+      if (ls == ESC_OK) ls = launch_write(L, w_wunits[w], cs);
+    }
     e = cudaStreamEndCapture(cs, &b->graph);
   }
   if (e == cudaSuccess && ls == ESC_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -2022,6 +2073,21 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
   *out = b;
   clear_error();
   return ESC_OK;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
+                             const esc_rows *rows, esc_batch **out) {
+  return batch_prepare(tables, preds, n, rows, 1, out);
+}
+
+esc_status esc_batch_prepare_waves(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
+                                   const esc_rows *rows, int32_t waves, esc_batch **out) {
+  return batch_prepare(tables, preds, n, rows, waves, out);
 }
 
 esc_status esc_batch_run(esc_batch *b, uint64_t *dev_counts, uint64_t *dev_done_ns, void *stream) {
@@ -2048,17 +2114,21 @@ esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred 
   if (s != ESC_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   s = esc_batch_run(b, nullptr, nullptr, st);
-  ScratchHdr h;
-  std::memset(&h, 0, sizeof h);
+  std::vector<uint8_t> hb(256 * (size_t)b->nwaves);
   if (s == ESC_OK) {
     cudaError_t e = cudaMemcpyAsync(counts, b->counts, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, b->scratch, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), b->scratch, hb.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = fail(ESC_ECUDA, std::string("esc_selectivity_batch: ") + cudaGetErrorString(e));
   }
+  const int nw = b->nwaves;
   batch_free(b);
   if (s != ESC_OK) return s;
-  if (h.status != 0) return device_status(h, "esc_selectivity_batch");
+  for (int w = 0; w < nw; ++w) {
+    ScratchHdr h;
+    std::memcpy(&h, hb.data() + 256 * (size_t)w, sizeof h);
+    if (h.status != 0) return device_status(h, "esc_selectivity_batch");
+  }
   bool trunc = false;
   if (rows)
     for (int i = 0; i < n; ++i) {

@@ -66,6 +66,8 @@ _sig = {
     "esc_selectivity_noalloc": ([_P, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(esc_rows), _P], _S),
     "esc_batch_prepare": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(esc_rows),
                            ctypes.POINTER(_P)], _S),
+    "esc_batch_prepare_waves": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(esc_rows),
+                                 ctypes.c_int32, ctypes.POINTER(_P)], _S),
     "esc_batch_run": ([_P, _P, _P, _P], _S),
     "esc_batch_destroy": ([_P], _S),
     "esc_selectivity_batch": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32,
@@ -246,6 +248,19 @@ def esc_batch_prepare(tables: Sequence[int], preds: Sequence[int], rows=None) ->
     else:
         arr, keep = _rows_array(rows)
         _check(_lib.esc_batch_prepare(ta, pa, n, arr, ctypes.byref(out)), "esc_batch_prepare")
+    return out.value
+
+
+def esc_batch_prepare_waves(tables: Sequence[int], preds: Sequence[int], rows=None, waves: int = 1) -> int:
+    n = len(tables)
+    ta = (_P * n)(*tables)
+    pa = (_P * n)(*preds)
+    out = _P()
+    if rows is None:
+        _check(_lib.esc_batch_prepare_waves(ta, pa, n, None, waves, ctypes.byref(out)), "esc_batch_prepare_waves")
+    else:
+        arr, keep = _rows_array(rows)
+        _check(_lib.esc_batch_prepare_waves(ta, pa, n, arr, waves, ctypes.byref(out)), "esc_batch_prepare_waves")
     return out.value
 
 

@@ -10,14 +10,21 @@ predicates and launches them: count requests on one table, when at least
 `shared_min` of them arrived together, share one pass over it
 (esc_selectivity_shared_async); the others run as one batch
 (esc_selectivity_batch_async).
-Waves on different streams overlap on the GPU.  A request's latency runs
-from its arrival to the host observing its wave's completion event.
+Waves on different streams overlap on the GPU.  A request's predicate is
+compiled on a small pool of host threads as soon as it arrives (the library
+call releases the interpreter lock), so the polling thread only admits,
+launches and observes completions.  A request's latency runs from its
+arrival to the host observing its wave's completion event.
+
+`PlainServer` is the baseline without batching: every request is its own
+sub-query call, launched when it arrives (round robin over the streams).
 """
 from __future__ import annotations
 
 import dataclasses
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 from typing import Callable, Deque, Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -35,6 +42,7 @@ class Request:
     count: Optional[int] = None
     done: Optional[float] = None
     rows: Optional[tuple] = None
+    pred: Optional[object] = None       # compiled predicate (a future while compiling)
 
 
 def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
@@ -83,7 +91,7 @@ def wave_groups(batch: Sequence[Request], shared_min: int) -> Tuple[List[List[Re
 
 class Server:
     def __init__(self, esc, tables, mem_budget: int = 8 << 30, max_batch: int = 512, streams: int = 2,
-                 device="cuda", shared_min: int = 8):
+                 device="cuda", shared_min: int = 8, compile_threads: int = 4):
         self.esc = esc
         self.tables = tables
         self.budget = mem_budget
@@ -96,6 +104,10 @@ class Server:
         self.waves = 0
         self.shared_min = shared_min      # count requests per table that share one pass
         self.shared_launches = 0
+        self.compile_threads = compile_threads
+
+    def _compile(self, r: Request):
+        return self.esc.Predicate(self.tables[r.table], r.text, tuple(r.proj))
 
     def run(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Request]:
         """Serves `requests` (arrival times relative to the start) and returns them completed."""
@@ -103,12 +115,15 @@ class Server:
         pending: Deque[Request] = deque()
         queue = deque(sorted(requests, key=lambda r: r.arrival))
         slots: List[Optional[dict]] = [None] * len(self.streams)
+        pool = ThreadPoolExecutor(self.compile_threads)
         t0 = clock()
         done_n = 0
         while done_n < len(requests):
             now = clock() - t0
             while queue and queue[0].arrival <= now:
-                pending.append(queue.popleft())
+                r = queue.popleft()
+                r.pred = pool.submit(self._compile, r)   # compiled off the polling thread
+                pending.append(r)
             progressed = False
             for k, st in enumerate(self.streams):
                 w = slots[k]
@@ -130,7 +145,8 @@ class Server:
                         self._launch(batch, k, st, nbytes, slots)
                         progressed = True
             if not progressed:
-                time.sleep(20e-6)
+                time.sleep(0)
+        pool.shutdown(wait=True)
         return list(requests)
 
     def _launch(self, batch: List[Request], k: int, st, nbytes: int, slots) -> None:
@@ -145,8 +161,8 @@ class Server:
             # outputs and counts are allocated (and zeroed) on the wave's own
             # stream, so that the kernels below are ordered after the fill
             for r in batch:
-                t = self.tables[r.table]
-                p = esc.Predicate(t, r.text, tuple(r.proj))
+                p = r.pred.result()
+                r.pred = p
                 preds.append(p)
                 if r.proj:
                     r.rows = p.alloc_rows(max(1, r.capacity), device=self.device)
@@ -185,3 +201,61 @@ def latency_summary(reqs: Sequence[Request]) -> Dict[str, float]:
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "throughput_per_s": len(reqs) / span}
+
+
+class PlainServer:
+    """One sub-query call per request, launched when it arrives (round robin
+    over `streams`); the baseline that continuous batching is measured
+    against.  Completion is observed by polling each request's event."""
+
+    def __init__(self, esc, tables, streams: int = 2, device="cuda", compile_threads: int = 4):
+        self.esc = esc
+        self.tables = tables
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        self.compile_threads = compile_threads
+
+    def run(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Request]:
+        esc = self.esc
+        queue = deque(sorted(requests, key=lambda r: r.arrival))
+        pool = ThreadPoolExecutor(self.compile_threads)
+        inflight: Deque[tuple] = deque()
+        compiling: Deque[Request] = deque()
+        t0 = clock()
+        done_n, k = 0, 0
+        while done_n < len(requests):
+            now = clock() - t0
+            progressed = False
+            while queue and queue[0].arrival <= now:
+                r = queue.popleft()
+                r.pred = pool.submit(lambda r=r: esc.Predicate(self.tables[r.table], r.text, tuple(r.proj)))
+                compiling.append(r)
+            while compiling and compiling[0].pred.done():
+                r = compiling.popleft()
+                r.pred = r.pred.result()
+                st = self.streams[k % len(self.streams)]
+                k += 1
+                with torch.cuda.stream(st):
+                    cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+                    if r.proj:
+                        r.rows = r.pred.alloc_rows(max(1, r.capacity), device=self.device)
+                    esc.esc_selectivity_async(self.tables[r.table].handle, r.pred.handle, cnt, r.rows, st)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                inflight.append((r, cnt, ev))
+                progressed = True
+            keep: Deque[tuple] = deque()
+            for item in inflight:
+                r, cnt, ev = item
+                if ev.query():
+                    r.count = int(cnt.item())
+                    r.done = clock() - t0
+                    done_n += 1
+                    progressed = True
+                else:
+                    keep.append(item)
+            inflight = keep
+            if not progressed:
+                time.sleep(0)
+        pool.shutdown(wait=True)
+        return list(requests)
