@@ -14,8 +14,6 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
-import hashlib
-import re
 import json
 import os
 import statistics
@@ -66,37 +64,15 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def source_digest() -> str:
-    """Digest of the scan and write kernels' code: comments removed and
-    whitespace collapsed, so that a comment edit keeps a profile valid."""
-    h = hashlib.sha256()
-    for p in ("paper_1901_01488_gb300/csrc/esc_scan.cu", "paper_1901_01488_gb300/csrc/esc_internal.h"):
-        with open(os.path.join(ROOT, p)) as f:
-            code = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
-        code = re.sub(r"//[^\n]*", " ", code)
-        h.update(" ".join(code.split()).encode())
-    return h.hexdigest()[:16]
-
-
-def profiled_traffic(key: str):
-    """A DRAM-bytes figure (`key`) from the committed ncu summary of this
-    workload, or None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "scan_kernel.skewed_60m_200preds.md")
-    try:
-        txt = open(path).read()
-    except OSError:
-        return None
-    vals = {}
-    for line in txt.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().split()[0].strip("`")
-    if vals.get("source_digest") != source_digest():
-        return None
-    try:
-        return float(vals[key])
-    except (KeyError, ValueError):
-        return None
+def profiled_traffic(key: str, rows: int):
+    """DRAM bytes per launch ("count": the scan kernel of a count call) or per
+    call ("call": scan + write of a materialising call) at `rows` rows, from
+    the committed small-case ncu summary scaled by rows (DRAM bytes per row
+    do not depend on the table size); None when the summary is missing or the
+    kernel source changed since it was captured."""
+    from paper_1901_01488_gb300 import ncu_profile
+    per_row = ncu_profile.traffic_per_row(key)
+    return None if per_row is None else per_row * rows
 
 
 class Clocks:
@@ -353,13 +329,13 @@ def run_esc(args):
             "hbm_gbs_algorithmic": step_gbs,
             "latency_ms": {"p50": p50, "p99": p99, "what": "device time of one sub-query call (events on its stream)"},
             "roofline": {"bound": "hbm", "achieved": scan_achieved, "peak": peak, "unit": "GB/s",
-                         "frac": scan_achieved / peak, "traffic": profiled_traffic("dram_bytes_per_launch"),
+                         "frac": scan_achieved / peak, "traffic": profiled_traffic("count", args.rows),
                          "kernel": "esc::scan_kernel", "peak_source": peak_src,
                          "measured_on": "the same 200 predicates counted (one launch per call: scan_kernel, or "
                                         "const_kernel for a program folded to a constant), CUDA events around each call",
                          "algorithmic_bytes_per_launch": sum(scan_bytes) / len(scan_bytes)},
             "roofline_call": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                              "frac": achieved / peak, "traffic": profiled_traffic("dram_bytes_per_call"),
+                              "frac": achieved / peak, "traffic": profiled_traffic("call", args.rows),
                               "kernels": "esc::scan_kernel + esc::write_kernel (one sub-query call, as timed)",
                               "algorithmic_bytes_per_call": sum(alg) / len(alg)},
             "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d,
@@ -659,46 +635,55 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- surrogate
 def run_surrogate(args):
-    """Learned surrogate: exact labels by batched ESC on a 2M-row table of the
-    skewed generator (the counts the parity tests check), MLP training on 90 %
-    of the pairs, q-error on the rest against per-column histograms under
-    independence."""
+    """Learned surrogate: exact labels by shared ESC scans on the 60M-row
+    skewed table, features from the compiled programs and a 1% sample's
+    per-column statistics, MLP training on 80 % of the pairs, calibration of
+    the exact-ESC fallback on 10 %, q-error on the last 10 % against the same
+    sample's statistics under independence (the method without the network)."""
     import numpy as np
     import torch
     from paper_1901_01488_gb300 import build as esc_build
     esc_build.build()
     from paper_1901_01488_gb300 import datagen, esc, surrogate as S
     dev = torch.device("cuda", 0)
-    nrows = 2_000_000 if args.rows == 60_000_000 else args.rows
+    nrows = args.rows
     t = datagen.skewed_table(nrows, seed=5, device=dev)
     table = esc.Table.from_datagen(t)
     n = args.pairs
     rng = np.random.default_rng(5)
     targets = 10.0 ** rng.uniform(-6, np.log10(0.9), n)
     t0 = time.perf_counter()
-    preds = [datagen.random_predicate(5_000_000 + j, float(targets[j])) for j in range(n)]
+    texts = [datagen.random_predicate(5_000_000 + j, float(targets[j])).text for j in range(n)]
     gen_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    counts = S.exact_counts(esc, table, preds)
+    counts = S.exact_counts(esc, table, texts)
     label_s = time.perf_counter() - t0
-    # device time of the labelling passes alone, on a 65,536-pair slice with predicates compiled beforehand
-    sl = preds[:65_536]
-    comp = [esc.Predicate(table, p.text) for p in sl]
-    dc = torch.zeros(len(comp), dtype=torch.int64, device=dev)
+    # device time of the labelling passes alone, on a 65,536-pair slice compiled beforehand
+    sl = texts[:65_536]
+    ps = esc.PredicateSet(table, sl)
+    dc = torch.zeros(len(sl), dtype=torch.int64, device=dev)
     st = torch.cuda.current_stream(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(st)
-    for s0 in range(0, len(comp), 2048):
-        ch = comp[s0:s0 + 2048]
-        esc.esc_selectivity_shared_async(table.handle, [p.handle for p in ch], dc[s0:s0 + len(ch)])
+    for s0 in range(0, len(sl), 2048):
+        h = ps.handles[s0:s0 + 2048]
+        esc.esc_selectivity_shared_async(table.handle, h, dc[s0:s0 + len(h)])
     b.record(st)
     torch.cuda.synchronize()
     dev_ms = a.elapsed_time(b)
-    assert dc.cpu().numpy().tolist() == counts[:len(comp)].tolist()
-    y = S.log_selectivity(counts, nrows)
-    X = S.encode_batch(preds)
-    ntr = int(0.9 * n)
+    assert dc.cpu().numpy().tolist() == counts[:len(sl)].tolist()
+    ps.close()
+    sample = max(10_000, nrows // 100)
+    syn = S.Synopsis({c.name: datagen.Column(c.name, c.dtype, c.data[:sample]).numpy() for c in t.columns},
+                     datagen.SKEWED_COLUMNS)
+    t0 = time.perf_counter()
+    L = S.listings(esc, table, texts)
+    X = syn.features_batch(L)
+    base = syn.base_log(L, nrows)
+    feat_s = time.perf_counter() - t0
+    y = (S.log_selectivity(counts, nrows) - base).astype(np.float32)
+    ntr, nva = int(0.8 * n), int(0.9 * n)
     model = S.Surrogate(esc, seed=3)
     xb, yb = S.to_bf16(X, "cuda"), torch.from_numpy(y).cuda()
     epochs = 20
@@ -708,31 +693,39 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     a.record(st)
-    est_log = model.predict(xb[ntr:])
+    est_log = model.predict(xb[nva:])
     b.record(st)
     torch.cuda.synchronize()
     pred_ms = a.elapsed_time(b)
-    est = 10.0 ** est_log.cpu().numpy().astype(np.float64) * nrows
-    q = S.qerror(est, counts[ntr:])
-    h = S.Histograms({c.name: c.numpy()[:500_000] for c in t.columns})
-    qi = S.qerror(np.array([S.independence_estimate(h, p) for p in preds[ntr:]]) * nrows, counts[ntr:])
+    est = 10.0 ** (base[nva:] + est_log.cpu().numpy().astype(np.float64)) * nrows
+    q = S.qerror(est, counts[nva:])
+    qi = S.qerror(np.array([syn.independence(l) for l in L[nva:]]) * nrows, counts[nva:])
+    fb = S.Fallback(model, tol=2.0, coverage=0.95)
+    fb.calibrate(xb[ntr:nva], base[ntr:nva], counts[ntr:nva], nrows)
+    est2, used = fb.estimate(xb[nva:], base[nva:],
+                             lambda idx: S.exact_counts(esc, table, [texts[nva + i] for i in idx]), nrows)
+    q2 = S.qerror(est2, counts[nva:])
     flops_per_sample = 2 * (64 * 128 + 128 * 128 + 128)
 
     def stats(x):
         return {"median": float(np.median(x)), "p95": float(np.percentile(x, 95)), "max": float(np.max(x))}
 
     out = {"metric": METRIC, "workload": "surrogate", "value": n / label_s, "unit": "exact labels/s",
-           "config": {"workload": f"{n:,} (predicate, exact count) pairs on a {nrows:,}-row skewed table "
-                                  f"(1-6 terms, selectivity 1e-6..0.9); MLP 64-128-128-1, bf16 weights, fp32 "
-                                  f"accumulate; 90/10 split", "data": "synthetic"},
+           "config": {"workload": f"{n:,} (predicate, exact count) pairs on the {nrows:,}-row skewed table "
+                                  f"(1-6 terms, selectivity 1e-6..0.9); features from the compiled programs and "
+                                  f"a {sample:,}-row sample; MLP 64-128-128-1, bf16 weights, fp32 accumulate; "
+                                  f"80/10/10 split (train / fallback calibration / held out)", "data": "synthetic"},
            "labels": {"wall_s": label_s, "per_s": n / label_s, "predicate_generation_s": gen_s,
-                      "device_ms_per_65536": dev_ms, "device_labels_per_s": len(comp) / (dev_ms / 1e3),
-                      "labels_by": "shared scans of 2048 predicates"},
+                      "device_ms_per_65536": dev_ms, "device_labels_per_s": len(sl) / (dev_ms / 1e3),
+                      "labels_by": "shared scans of 2048 predicates", "features_s": feat_s},
            "training": {"epochs": epochs, "samples": ntr, "wall_s": train_s, "loss_first_last": [curve[0], curve[-1]],
                         "samples_per_s": ntr * epochs / train_s},
-           "inference": {"samples": n - ntr, "ms": pred_ms, "samples_per_s": (n - ntr) / (pred_ms / 1e3),
-                         "gflops": (n - ntr) * flops_per_sample / (pred_ms / 1e3) / 1e9},
-           "qerror_surrogate": stats(q), "qerror_independence": stats(qi)}
+           "inference": {"samples": n - nva, "ms": pred_ms, "samples_per_s": (n - nva) / (pred_ms / 1e3),
+                         "gflops": (n - nva) * flops_per_sample / (pred_ms / 1e3) / 1e9},
+           "qerror_surrogate": stats(q), "qerror_independence": stats(qi),
+           "fallback": {"tolerance": 2.0, "exact_fraction": float(used.mean()), "qerror": stats(q2),
+                        "within_tolerance": float(np.mean(q2 <= 2.0)),
+                        "trusted_decades": sorted(k for k, v in fb.trusted.items() if v)}}
     print(json.dumps(out), flush=True)
 
 

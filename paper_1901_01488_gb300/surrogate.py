@@ -2,73 +2,192 @@
 
 Not in the paper: the paper computes every selectivity exactly (Sec. 2).
 This module adds a small network that *estimates* log10 selectivity from
-the predicate alone, trained on (predicate, exact count) pairs that ESC
-itself produces; exact ESC stays the reference (q-error) and the fallback, and
-is the only source of counts a planner may treat as exact.
+the compiled predicate, trained on (predicate, exact count) pairs that ESC
+itself produces; exact ESC stays the reference (q-error) and the fallback,
+and is the only source of counts a planner may treat as exact.
 
-* encode(): 64 features = 8 column slots x [present, lo, hi, is_eq, is_in,
-  in_size / 16, in_or_pair, is_udf], bounds normalised to the column domain.
+* Synopsis: per-column statistics of a table sample (sorted values), the
+  estimator ESC replaces.  `Synopsis.independence(listing)` evaluates a
+  compiled program (its listing from esc_predicate_explain: the merged,
+  domain-clamped tests the kernel runs) with each test's sample selectivity,
+  AND as a product, OR as a + b - ab, NOT as 1 - a.
+* `Synopsis.features(listing)`: 64 features from the same listing -- for
+  each of 8 column slots [tested, log10 of its tests' sample selectivity,
+  lo, hi (normalised to the column's sample range), set size / 16, under an
+  OR, udf operand] (7 per slot), and 8 global ones (log10 of the
+  independence estimate, tests, ORs, NOTs, udf, set tests).  The network learns the
+  correction independence misses (correlated columns, udf terms).
 * Surrogate: the MLP 64 -> 128 -> 128 -> 1 of libesc (esc_mlp_forward,
   esc_mlp_grad, esc_mlp_adam); float32 master weights, bfloat16 copies.
-* independence_estimate(): the synopsis approach ESC replaces (per-column
-  histograms combined under independence), as the comparison point.
+* `Fallback`: the surrogate where its held-out error is small (calibrated
+  per predicted-selectivity bucket), exact ESC otherwise.
 """
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 import torch
 
-from . import datagen
-
 NFEAT = 64
-SLOTS = datagen.SKEWED_COLUMNS          # key, code150, code25, code7, day, price, qty, key2
+NSLOT = 8
+PER_SLOT = 7
+LOG_FLOOR = -8.0          # log10 selectivity floor of the features (an empty test)
 
 
-def _norm(col: str, v: float) -> float:
-    _, lo, hi = datagen.SKEWED_SCHEMA[col]
-    return min(1.0, max(0.0, (v - lo) / max(1, hi - lo)))
+def _parse(listing: str):
+    """(ref slot -> column name, instructions as token lists) of a program listing."""
+    refs, code = {}, []
+    for line in listing.splitlines():
+        f = line.split()
+        if not f:
+            continue
+        if f[0] == "ref":
+            refs[int(f[1])] = f[2]
+        elif f[0] == "instr":
+            code.append(f[2:])
+    return refs, code
 
 
-def encode(pred: datagen.Predicate) -> np.ndarray:
-    f = np.zeros(NFEAT, dtype=np.float32)
-    have = np.zeros(len(SLOTS), dtype=bool)
+class Synopsis:
+    """Per-column statistics of a table sample (every value kept, sorted):
+    the selectivity of a range, an equality or a set on one column, exact on
+    the sample."""
 
-    def put(t: datagen.Term, in_or: bool):
-        if t.kind == "udf":
-            s = SLOTS.index("price")
-            lo, hi = (t.lo + 1) / datagen.UDF_MODULUS, 1.0
-        elif t.kind == "in":
-            s = SLOTS.index(t.col)
-            lo, hi = _norm(t.col, min(t.values)), _norm(t.col, max(t.values))
-        else:
-            s = SLOTS.index(t.col)
-            lo, hi = _norm(t.col, t.lo), _norm(t.col, t.hi if t.kind == "range" else t.lo)
-        b = 8 * s
-        if have[s]:                       # several terms on one column: intersect
-            lo, hi = max(lo, f[b + 1]), min(hi, f[b + 2])
-        have[s] = True
-        f[b + 0] = 1.0
-        f[b + 1], f[b + 2] = lo, hi
-        f[b + 3] = max(f[b + 3], float(t.kind == "eq"))
-        f[b + 4] = max(f[b + 4], float(t.kind == "in"))
-        f[b + 5] = max(f[b + 5], len(t.values) / 16.0)
-        f[b + 6] = max(f[b + 6], float(in_or))
-        f[b + 7] = max(f[b + 7], float(t.kind == "udf"))
+    def __init__(self, host_cols: Dict[str, np.ndarray], slots: Sequence[str]):
+        self.slots = list(slots)[:NSLOT]
+        self.sorted = {c: np.sort(np.asarray(a).astype(np.int64)) for c, a in host_cols.items()}
+        self.n = len(next(iter(self.sorted.values())))
+        self.lo = {c: int(v[0]) if len(v) else 0 for c, v in self.sorted.items()}
+        self.hi = {c: int(v[-1]) if len(v) else 0 for c, v in self.sorted.items()}
 
-    for t in pred.terms:
-        if t.kind == "or":
-            for part in t.parts:
-                put(part, True)
-        else:
-            put(t, False)
-    return f
+    def range_sel(self, c: str, a: int, b: int) -> float:
+        if a > b or self.n == 0:
+            return 0.0
+        v = self.sorted[c]
+        return float(np.searchsorted(v, b, "right") - np.searchsorted(v, a, "left")) / self.n
 
+    def set_sel(self, c: str, vals: Sequence[int]) -> float:
+        return min(1.0, sum(self.range_sel(c, v, v) for v in set(vals)))
 
-def encode_batch(preds: Sequence[datagen.Predicate]) -> np.ndarray:
-    return np.stack([encode(p) for p in preds]) if preds else np.zeros((0, NFEAT), np.float32)
+    @staticmethod
+    def udf_sel(m: int, a: int, b: int) -> float:
+        """Remainders of non-negative products taken as uniform on 0..m-1."""
+        lo, hi = max(a, 0), min(b, m - 1)
+        return max(0, hi - lo + 1) / m
+
+    def _test(self, refs, ins) -> Tuple[float, Optional[str], dict]:
+        op = ins[0]
+        if op == "RANGE":
+            c = refs[int(ins[1])]
+            return self.range_sel(c, int(ins[3]), int(ins[4])), c, {"lo": int(ins[3]), "hi": int(ins[4])}
+        if op == "IN":
+            c = refs[int(ins[1])]
+            vals = [int(v) for v in ins[3].split(",")] if len(ins) > 3 else []
+            return self.set_sel(c, vals), c, {"lo": min(vals, default=0), "hi": max(vals, default=0),
+                                              "set": len(vals)}
+        if op == "UDF":
+            c, c2 = refs[int(ins[1])], refs[int(ins[3])]
+            return self.udf_sel(int(ins[5]), int(ins[6]), int(ins[7])), c, {"udf": c2}
+        return 0.0, None, {}
+
+    def _walk(self, listing: str):
+        """Evaluates the program on selectivities; also collects, per column,
+        the tests it makes (with whether they sit under an OR)."""
+        refs, code = _parse(listing)
+        stack: List[Tuple[float, List[int]]] = []   # (selectivity, indices of the tests below)
+        tests = []                                   # (column, selectivity, info, under_or)
+        nor = nnot = 0
+        for ins in code:
+            op = ins[0]
+            if op in ("RANGE", "IN", "UDF"):
+                sel, c, info = self._test(refs, ins)
+                tests.append([c, sel, info, False])
+                stack.append((sel, [len(tests) - 1]))
+            elif op == "TRUE":
+                stack.append((1.0, []))
+            elif op == "FALSE":
+                stack.append((0.0, []))
+            elif op == "NOT":
+                a, ta = stack.pop()
+                stack.append((1.0 - a, ta))
+                nnot += 1
+            elif op in ("AND", "OR"):
+                b, tb = stack.pop()
+                a, ta = stack.pop()
+                if op == "AND":
+                    stack.append((a * b, ta + tb))
+                else:
+                    for t in ta + tb:
+                        tests[t][3] = True
+                    stack.append((a + b - a * b, ta + tb))
+                    nor += 1
+            # JZ / JNZ only skip work whose result is decided: no effect on the value
+        sel = stack[-1][0] if stack else 1.0
+        return min(1.0, max(0.0, sel)), tests, nor, nnot
+
+    def independence(self, listing: str) -> float:
+        return self._walk(listing)[0]
+
+    def features(self, listing: str) -> np.ndarray:
+        """Per slot: [tested, log10 of its tests' selectivity (sample, as if
+        independent), lo, hi (of its range / set tests, normalised to the
+        column's sample range), set size / 16, under an OR, udf operand];
+        then [log10 of the independence estimate, tests / 8, ORs / 4,
+        NOTs / 4, has a udf, set tests / 4, 0, 0].  Logs are scaled by 1/8."""
+        sel, tests, nor, nnot = self._walk(listing)
+        f = np.zeros(NFEAT, dtype=np.float32)
+
+        def lg(x):
+            return max(LOG_FLOOR, math.log10(max(x, 1e-300))) / -LOG_FLOOR
+
+        per: Dict[str, List] = {}
+        for c, s_, info, under_or in tests:
+            per.setdefault(c, []).append((s_, info, under_or))
+            if "udf" in info and info["udf"] in self.slots:
+                f[PER_SLOT * self.slots.index(info["udf"]) + 6] = 1.0
+        for c, lst in per.items():
+            if c not in self.slots:
+                continue
+            b = PER_SLOT * self.slots.index(c)
+            span = max(1, self.hi[c] - self.lo[c])
+            prod, lo, hi = 1.0, 1.0, 0.0
+            for s_, info, under_or in lst:
+                prod *= s_
+                if "lo" in info:
+                    lo = min(lo, (info["lo"] - self.lo[c]) / span)
+                    hi = max(hi, (info["hi"] - self.lo[c]) / span)
+                if "set" in info:
+                    f[b + 4] = max(f[b + 4], info["set"] / 16.0)
+                if "udf" in info:
+                    f[b + 6] = 1.0
+                if under_or:
+                    f[b + 5] = 1.0
+            f[b + 0] = 1.0
+            f[b + 1] = lg(prod)
+            if hi >= lo:
+                f[b + 2] = min(1.0, max(0.0, lo))
+                f[b + 3] = min(1.0, max(0.0, hi))
+        g = PER_SLOT * NSLOT
+        f[g + 0] = lg(sel)
+        f[g + 1] = len(tests) / 8.0
+        f[g + 2] = nor / 4.0
+        f[g + 3] = nnot / 4.0
+        f[g + 4] = float(any("udf" in t[2] for t in tests))
+        f[g + 5] = float(sum(1 for t in tests if "set" in t[2])) / 4.0
+        return f
+
+    def features_batch(self, listings: Sequence[str]) -> np.ndarray:
+        if not listings:
+            return np.zeros((0, NFEAT), np.float32)
+        return np.stack([self.features(l) for l in listings])
+
+    def base_log(self, listings: Sequence[str], nrows: int) -> np.ndarray:
+        """log10 selectivity of the independence estimate, clamped like a
+        label (at least one row): the network learns the correction to it."""
+        est = np.array([self.independence(l) for l in listings], dtype=np.float64) * nrows
+        return log_selectivity(est, nrows)
 
 
 def to_bf16(x: np.ndarray, device) -> torch.Tensor:
@@ -77,7 +196,8 @@ def to_bf16(x: np.ndarray, device) -> torch.Tensor:
 
 
 def log_selectivity(counts: np.ndarray, nrows: int) -> np.ndarray:
-    return np.log10(np.maximum(counts, 1) / float(nrows)).astype(np.float32)
+    """log10 of the selectivity, counts clamped to at least one row."""
+    return np.log10(np.maximum(np.asarray(counts, dtype=np.float64), 1.0) / float(nrows)).astype(np.float32)
 
 
 def qerror(est: np.ndarray, true: np.ndarray) -> np.ndarray:
@@ -87,19 +207,18 @@ def qerror(est: np.ndarray, true: np.ndarray) -> np.ndarray:
     return np.maximum(e / t, t / e)
 
 
-def exact_counts(esc, table, preds: Sequence[datagen.Predicate], chunk: int = 2048, stream=None) -> np.ndarray:
+def exact_counts(esc, table, texts: Sequence[str], chunk: int = 2048, stream=None) -> np.ndarray:
     """Exact ESC counts of many predicates on one table: each chunk compiled
     in one call (host threads), one shared pass per chunk
     (esc_selectivity_shared_async), counts read back once at the end."""
-    n = len(preds)
+    n = len(texts)
     dev = torch.zeros(max(1, n), dtype=torch.int64, device="cuda")
     keep = []
     for s in range(0, n, chunk):
-        ps = esc.PredicateSet(table, [p.text for p in preds[s:s + chunk]])
+        ps = esc.PredicateSet(table, list(texts[s:s + chunk]))
         esc.esc_selectivity_shared_async(table.handle, ps.handles, dev[s:s + len(ps)], stream=stream)
         keep.append(ps)  # predicates stay alive until their pass has run
-    out = dev[:n].cpu().numpy().astype(np.int64)
-    return out
+    return dev[:n].cpu().numpy().astype(np.int64)
 
 
 class Surrogate:
@@ -162,55 +281,50 @@ class Surrogate:
         self.step = int(st["step"])
 
 
-# ---------------------------------------------------------------- synopsis baseline
-class Histograms:
-    """Per-column statistics of a table sample: exact frequencies for columns
-    with at most 2^24 values, used under the independence assumption."""
-
-    def __init__(self, host_cols: Dict[str, np.ndarray]):
-        self.n = len(next(iter(host_cols.values())))
-        self.freq = {}
-        for c, a in host_cols.items():
-            kind, lo, hi = datagen.SKEWED_SCHEMA[c]
-            if hi - lo < (1 << 24) + 1:
-                self.freq[c] = np.cumsum(np.bincount(a.astype(np.int64) - lo, minlength=hi - lo + 1)) / self.n
-            else:                                            # wide: 4096 equal-width buckets
-                edges = np.linspace(lo, hi + 1, 4097)
-                h, _ = np.histogram(a, bins=edges)
-                self.freq[c] = (edges, np.cumsum(h) / self.n)
-
-    def range_sel(self, c: str, a: int, b: int) -> float:
-        _, lo, hi = datagen.SKEWED_SCHEMA[c]
-        a, b = max(a, lo), min(b, hi)
-        if a > b:
-            return 0.0
-        f = self.freq[c]
-        if isinstance(f, tuple):
-            edges, cum = f
-            def at(x):   # fraction of rows <= x, linear inside a bucket
-                i = int(np.searchsorted(edges, x, side="right")) - 1
-                i = min(max(i, 0), len(cum) - 1)
-                prev = cum[i - 1] if i > 0 else 0.0
-                return prev + (cum[i] - prev) * (x + 1 - edges[i]) / (edges[i + 1] - edges[i])
-            return max(0.0, at(b) - at(a - 1))
-        return float(f[b - lo] - (f[a - lo - 1] if a > lo else 0.0))
-
-    def term_sel(self, t: datagen.Term) -> float:
-        if t.kind == "eq":
-            return self.range_sel(t.col, t.lo, t.lo)
-        if t.kind == "range":
-            return self.range_sel(t.col, t.lo, t.hi)
-        if t.kind == "in":
-            return min(1.0, sum(self.range_sel(t.col, v, v) for v in set(t.values)))
-        if t.kind == "udf":
-            m = datagen.UDF_MODULUS
-            return (m - 1 - t.lo) / m
-        a, b = self.term_sel(t.parts[0]), self.term_sel(t.parts[1])
-        return a + b - a * b
+def listings(esc, table, texts: Sequence[str], chunk: int = 4096) -> List[str]:
+    """Program listings of many predicates (compiled in one call per chunk)."""
+    out: List[str] = []
+    for s in range(0, len(texts), chunk):
+        ps = esc.PredicateSet(table, list(texts[s:s + chunk]))
+        out.extend(esc.esc_predicate_explain(h) for h in ps.handles)
+        ps.close()
+    return out
 
 
-def independence_estimate(h: Histograms, pred: datagen.Predicate) -> float:
-    s = 1.0
-    for t in pred.terms:
-        s *= h.term_sel(t)
-    return s
+class Fallback:
+    """Estimates with exact ESC as the fallback: the surrogate's estimate
+    (base + the network's correction, in log10 selectivity) is used where the
+    calibration set says its q-error stays within `tol` for `coverage` of the
+    predicates of that predicted-selectivity decade; elsewhere the count comes
+    from exact ESC."""
+
+    def __init__(self, model: "Surrogate", tol: float = 2.0, coverage: float = 0.95):
+        self.model = model
+        self.tol = tol
+        self.coverage = coverage
+        self.trusted: Dict[int, bool] = {}
+
+    @staticmethod
+    def bucket(log_sel: float) -> int:
+        return int(math.floor(max(LOG_FLOOR, min(0.0, log_sel))))
+
+    def predict_log(self, x_bf16: torch.Tensor, base: np.ndarray) -> np.ndarray:
+        return base + self.model.predict(x_bf16).cpu().numpy().astype(np.float64)
+
+    def calibrate(self, x_bf16: torch.Tensor, base: np.ndarray, counts: np.ndarray, nrows: int) -> Dict[int, bool]:
+        pred = self.predict_log(x_bf16, base)
+        q = qerror(10.0 ** pred * nrows, counts)
+        for b in set(self.bucket(v) for v in pred):
+            sel = np.array([self.bucket(v) == b for v in pred])
+            self.trusted[b] = bool(sel.sum() >= 20 and np.mean(q[sel] <= self.tol) >= self.coverage)
+        return self.trusted
+
+    def estimate(self, x_bf16: torch.Tensor, base: np.ndarray, exact_fn, nrows: int) -> Tuple[np.ndarray, np.ndarray]:
+        """(row estimates, used_exact mask): exact_fn(indices) -> exact counts."""
+        pred = self.predict_log(x_bf16, base)
+        use_exact = np.array([not self.trusted.get(self.bucket(v), False) for v in pred])
+        est = 10.0 ** pred * nrows
+        idx = np.flatnonzero(use_exact)
+        if len(idx):
+            est[idx] = np.asarray(exact_fn(idx), dtype=np.float64)
+        return est, use_exact
