@@ -459,7 +459,8 @@ def run_batch(args):
                                             "completion = an event after each call"},
            "bit_exact_vs_one_launch_per_query": same, "gpu_launches_per_batch": {"1": 2, str(WAVES): 2 * WAVES},
            "autotuner": {"classes": len(tuner.cache),
-                         "choices (max_tile_rows, max_unit_kb, units_per_sm)": sorted(set(tuner.cache.values()))}}
+                         "choices (max_tile_rows, max_unit_kb, units_per_sm, consumer_warps, rows_per_pass)":
+                             sorted(set(tuner.cache.values()))}}
     print(json.dumps(out), flush=True)
     for b in batches.values():
         esc.esc_batch_destroy(b)

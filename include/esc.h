@@ -141,17 +141,32 @@ esc_status esc_predicate_compile_many(const esc_table *table, const char *const 
  * bytes per work unit (16..4096; a unit is a run of tiles claimed with one
  * ticket; the last tiles of a table always go out one per unit);
  * units_per_sm: work units to aim for per SM (1..64; more balances load,
- * fewer amortises per-unit work).  Defaults: 32768, 512, 8.  Results never
- * depend on these. */
+ * fewer amortises per-unit work).  consumer_warps and rows_per_pass pick the
+ * scan kernel's block shape: the warps per CTA that evaluate (the CTA has
+ * one more, the copy warp) and the rows each lane evaluates per decoded
+ * program instruction (8 per 256-row group, one or two groups per pass).
+ * The shapes compiled are (15, 16) and (19, 8), which run every program,
+ * and (19, 16) and (23, 8), which run programs without a udf.  (0, 0) is
+ * automatic: a program reading more than 20 bytes per row runs (19, 8) if
+ * it has a udf, else (23, 8); a narrower one (15, 16) or (19, 16).
+ * Defaults: 32768, 512, 8, 0, 0.  A batch (esc_batch_prepare,
+ * esc_selectivity_batch) uses its queries' tile and unit sizes, but its
+ * queries share a launch, so each launch takes the automatic shape: with
+ * the udf path if any of its programs has a udf, and the wide form if
+ * programs reading more than 20 bytes per row hold most of its bytes.
+ * Results never depend on any of these. */
 typedef struct esc_tuning {
     uint32_t max_tile_rows;
     uint32_t max_unit_kb;
     int32_t units_per_sm;
-    int32_t reserved;
+    uint16_t consumer_warps;
+    uint16_t rows_per_pass;
 } esc_tuning;
 
 /* Sets (tuning NULL: restores the defaults) or reads a predicate's launch
- * shape.  ESC_EINVAL for values outside the ranges above.  Not thread-safe
+ * shape.  ESC_EINVAL for values outside the ranges above, for a block shape
+ * that is not compiled, and for a shape without the udf path on a program
+ * with a udf; the predicate's tuning is then unchanged.  Not thread-safe
  * against concurrent calls that use the same predicate. */
 esc_status esc_predicate_set_tuning(esc_pred *pred, const esc_tuning *tuning);
 esc_status esc_predicate_get_tuning(const esc_pred *pred, esc_tuning *out);

@@ -952,8 +952,13 @@ esc_status esc_predicate_set_tuning(esc_pred *p, const esc_tuning *t) {
     return fail(ESC_EINVAL, "esc_predicate_set_tuning: max_unit_kb must be in 16..4096");
   if (t->units_per_sm < 1 || t->units_per_sm > 64)
     return fail(ESC_EINVAL, "esc_predicate_set_tuning: units_per_sm must be in 1..64");
+  bool udf = false;
+  for (const Instr &I : p->code) udf = udf || I.op == OP_UDF;
+  if (scan_shape_for(t->consumer_warps, t->rows_per_pass, udf, 0) < 0)
+    return fail(ESC_EINVAL, "esc_predicate_set_tuning: no compiled scan shape has " + std::to_string(t->consumer_warps) +
+                                " consumer warps and " + std::to_string(t->rows_per_pass) + " rows per pass" +
+                                (udf ? " with the udf path" : ""));
   p->tuning = *t;
-  p->tuning.reserved = 0;
   clear_error();
   return ESC_OK;
 }

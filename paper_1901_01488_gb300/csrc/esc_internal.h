@@ -26,6 +26,36 @@ constexpr int kGroup = 256;     // rows per warp group (32 lanes x 8 rows)
 constexpr int kMaxTileRows = 32768;
 constexpr int kMaxUnitRows = 65536;   // rows per scan work unit at most, and per compaction unit
 
+// Block shapes of the scan kernel, one compiled instance each: consumer
+// warps per CTA, 256-row groups each warp evaluates per decoded instruction
+// (8 rows per lane per group), and whether the instance has the udf path
+// (whose registers limit how many warps fit).
+struct ScanShape {
+  int consumers;
+  int groups;
+  bool udf;
+};
+constexpr ScanShape kScanShapes[] = {{15, 2, true}, {19, 2, false}, {19, 1, true}, {23, 1, false}};
+constexpr int kNumScanShapes = 4;
+// Automatic choice, from per-predicate timings of the four shapes on a
+// 60M-row table: programs reading more than kWideBytes bytes per row run
+// faster with one group per pass and more warps (their many loads and
+// tests need latency hiding more than fewer decodes); narrower ones with two
+// groups per pass; a udf needs an instance with the udf path.
+constexpr uint32_t kWideBytes = 20;
+inline int auto_scan_shape(bool has_udf, bool wide) { return has_udf ? (wide ? 2 : 0) : (wide ? 3 : 1); }
+// The shape a tuning asks for (consumer_warps, rows_per_pass), for a program
+// with or without a udf reading `read_bytes` bytes per row: its index, the
+// automatic one for (0, 0), or -1 when no compiled shape matches.
+inline int scan_shape_for(uint32_t consumer_warps, uint32_t rows_per_pass, bool has_udf, uint32_t read_bytes) {
+  if (consumer_warps == 0 && rows_per_pass == 0) return auto_scan_shape(has_udf, read_bytes > kWideBytes);
+  for (int i = 0; i < kNumScanShapes; ++i)
+    if ((uint32_t)kScanShapes[i].consumers == consumer_warps && 8u * (uint32_t)kScanShapes[i].groups == rows_per_pass &&
+        (kScanShapes[i].udf || !has_udf))
+      return i;
+  return -1;
+}
+
 // Lane l of a warp owns, in a 256-row group, the rows
 //   64*j + 2*l + i   for j in 0..3, i in 0..1;
 // its 8-bit mask has bit 2*j + i for that row.  Each of the 4 loads per
@@ -155,7 +185,7 @@ struct esc_table {
 
 struct esc_pred {
   const esc_table *table;
-  esc_tuning tuning{32768u, 512u, 8, 0};
+  esc_tuning tuning{32768u, 512u, 8, 0, 0};
   std::string text;
   int32_t ninstr = 0;
   std::vector<int32_t> ref_cols;    // table column index of each stage slot
@@ -177,7 +207,7 @@ esc_status device_status(const ScratchHdr &h, const char *where);
 // (esc_debug_fail_allocs counts them down).
 bool inject_alloc_failure();
 // Defaults of esc_tuning.
-constexpr esc_tuning kDefaultTuning{32768u, 512u, 8, 0};
+constexpr esc_tuning kDefaultTuning{32768u, 512u, 8, 0, 0};
 // Fills the static part of a Query (program, read columns, projection) for a pred.
 void fill_query_program(const esc_pred *p, Query *q);
 // Granlund-Montgomery unsigned magic for divisor d (Fig. 4.1 of their paper).

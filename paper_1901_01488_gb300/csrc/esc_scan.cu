@@ -5,17 +5,18 @@
 // counts of esc_semijoin.cu).
 //
 // Kernel shape (sm_103a):
-//  * scan_kernel, persistent: one CTA per SM, 1 producer warp + kConsumers
-//    consumer warps (kConsumersLean in the instance for programs without a
-//    udf, whose register demand is lower); work units (a few consecutive
-//    tiles; the last tiles of a query one per unit) are claimed in order
-//    from a global ticket;
+//  * scan_kernel, persistent: one CTA per SM, 1 producer warp + 15 to 23
+//    consumer warps (one instance per block shape of kScanShapes: fewer
+//    warps where the udf path's registers are compiled in, more with one
+//    group per pass); work units (a few consecutive tiles; the last tiles of
+//    a query one per unit) are claimed in order from a global ticket;
 //  * the producer stages every column the predicate reads into shared memory
 //    with 1-D bulk TMA copies (cp.async.bulk ... mbarrier::complete_tx) into a
 //    ring of kStages stages; the ragged tail of the last tile (< 16 bytes per
 //    column) is copied with plain loads;
-//  * consumers claim pairs of 256-row groups of a stage from a shared counter
-//    and interpret the postfix program on 8 rows per lane, keeping the
+//  * consumers claim runs of one or two 256-row groups of a stage from a
+//    shared counter and interpret the postfix program on 8 rows per lane per
+//    group (one decode per instruction for the run), keeping the
 //    boolean evaluation stack as 8-bit masks in one 64-bit register;
 //  * counts: popc per lane, one atomic per warp and query;
 //  * ordered compaction, first pass: the selection bitmap (lane-major),
@@ -39,13 +40,12 @@
 
 namespace esc {
 
-constexpr int kConsumers = 15;                   // consumer warps per CTA
+constexpr int kConsumers = 15;                   // consumer warps per CTA of the shared scan
 constexpr int kThreads = 32 * (kConsumers + 1);  // + the producer warp: 16 warps, 4 per SM sub-partition
-// Programs without a udf: the udf remainder sets the kernel's register
-// demand (128 per thread), so a second instance of the scan kernel without
-// it runs more consumer warps per SM.
-constexpr int kConsumersLean = 19;
-constexpr int kThreadsLean = 32 * (kConsumersLean + 1);
+// The scan kernel's instances are the block shapes of kScanShapes: the udf
+// remainder sets the register demand (128 per thread at 16 warps, two groups
+// per pass), so the instances without it, or with one group per pass, run
+// more consumer warps per SM.
 constexpr int kStages = 3;
 constexpr uint32_t kStageBytes = 64 * 1024;
 constexpr int kTailTilesPerSm = 8;      // single-tile work units at the end of a query (per SM)
@@ -599,7 +599,7 @@ __device__ __forceinline__ bool stage_in_bounds(const Query *Q, int ngroups, Scr
 // (evaluate; count; compaction: bitmap words and unit totals; bitmap mode:
 // the caller's bitmap words).
 // NC consumer warps; UDF: the instance can run programs with a udf.
-template <int NC, bool UDF>
+template <int NC, bool UDF, int NG>
 __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *stages = smem + SmemLayout::stages;
@@ -764,11 +764,11 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
     const uint32_t r0 = mt.tile * Q->tile_rows;
     acc_q = mt.q;
     acc_ptr = Q->count;
-    // Consumers claim pairs of adjacent groups of the stage from a shared
+    // Consumers claim runs of NG adjacent groups of the stage from a shared
     // counter until none is left, then move on to the next stage: the work of
     // a stage spreads over every consumer whatever its group count, and a warp
     // that finishes early starts on the next stage.
-    const int npairs = (ngroups + 1) >> 1;
+    const int nruns = (ngroups + NG - 1) / NG;
     auto claim = [&]() {
       int j = 0;
       if (lane == 0) j = (int)atomicAdd(&take[s], 1u);
@@ -780,14 +780,17 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       const uint32_t nwords = (Q->nrows + 31u) / 32u;
       uint32_t *bm = Q->bitmap;
       uint32_t *rbm = reinterpret_cast<uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
-      for (int j = claim(); j < npairs; j = claim()) {
-        const int g = 2 * j, g1 = g + 1;
-        const int gs[2] = {g, g1 < ngroups ? g1 : g};
-        uint32_t mm[2];
-        eval_groups<2, UDF>(Q, stage, gs, lane, mm);
+      for (int j = claim(); j < nruns; j = claim()) {
+        // the run's groups; past the stage's last group, that group again
+        // (evaluated, not counted)
+        int gs[NG];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (i == 1 && g1 >= ngroups) break;
+        for (int i = 0; i < NG; ++i) gs[i] = min(NG * j + i, ngroups - 1);
+        uint32_t mm[NG];
+        eval_groups<NG, UDF>(Q, stage, gs, lane, mm);
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+          if (NG * j + i >= ngroups) break;
           const uint32_t m = mm[i] & valid_mask(gs[i], lane, rows);
           const uint32_t c = __popc(m);
           acc += c;
@@ -1511,6 +1514,49 @@ size_t smem_bytes() { return SmemLayout::total; }
       return fail(ESC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
   } while (0)
 
+// The scan kernel instance of block shape S (an index into kScanShapes).
+template <int S>
+struct ScanInstance {
+  static constexpr ScanShape sh = kScanShapes[S];
+  static constexpr int threads = 32 * (sh.consumers + 1);
+  static const void *fn() { return reinterpret_cast<const void *>(scan_kernel<sh.consumers, sh.udf, sh.groups>); }
+  static void launch(uint32_t grid, const Launch &L, cudaStream_t st) {
+    scan_kernel<sh.consumers, sh.udf, sh.groups><<<grid, threads, smem_bytes(), st>>>(L);
+  }
+};
+static_assert(kNumScanShapes == 4, "one ScanInstance per shape below");
+
+// Launches the scan kernel instance of block shape `shape`.
+void launch_scan_shape(int shape, uint32_t grid, const Launch &L, cudaStream_t st) {
+  switch (shape) {
+    case 0: ScanInstance<0>::launch(grid, L, st); break;
+    case 1: ScanInstance<1>::launch(grid, L, st); break;
+    case 2: ScanInstance<2>::launch(grid, L, st); break;
+    default: ScanInstance<3>::launch(grid, L, st); break;
+  }
+}
+
+// Kernel attributes (dynamic shared memory) of every kernel of this file,
+// and the CTAs per SM that every scan instance reaches.
+esc_status configure_kernels(int *blocks_per_sm) {
+  const void *fns[kNumScanShapes] = {ScanInstance<0>::fn(), ScanInstance<1>::fn(), ScanInstance<2>::fn(),
+                                     ScanInstance<3>::fn()};
+  const int threads[kNumScanShapes] = {ScanInstance<0>::threads, ScanInstance<1>::threads, ScanInstance<2>::threads,
+                                       ScanInstance<3>::threads};
+  int b = 1 << 30;
+  for (int i = 0; i < kNumScanShapes; ++i) {
+    ESC_CK(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+    int k = 0;
+    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fns[i], threads[i], smem_bytes()));
+    b = std::min(b, k);
+  }
+  if (b < 1) return fail(ESC_ECUDA, "a scan kernel instance does not fit on an SM");
+  ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
+  ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
+  *blocks_per_sm = b;
+  return ESC_OK;
+}
+
 }  // namespace
 
 esc_status device_state(DeviceState **out) {
@@ -1521,19 +1567,8 @@ esc_status device_state(DeviceState **out) {
   DeviceState &d = g_dev[dev];
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumers, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes()));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumersLean, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes()));
-    ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
-    ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel<kConsumers, true>, kThreads,
-                                                         smem_bytes()));
-    if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
-    int lean = 0;
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lean, scan_kernel<kConsumersLean, false>, kThreadsLean,
-                                                         smem_bytes()));
-    if (lean < d.blocks_per_sm) return fail(ESC_ECUDA, "scan kernel (no udf) does not fit on an SM");
+    esc_status cs = configure_kernels(&d.blocks_per_sm);
+    if (cs != ESC_OK) return cs;
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
@@ -1552,16 +1587,44 @@ esc_status device_state(DeviceState **out) {
 // 256-row group, at most kMaxTileRows.
 // The value of a program that reads no column (TRUE, FALSE and connectives
 // only); false when the program reads a column.
-// Whether the program has a udf test: it then needs the scan kernel's udf
-// instance; every other program runs on the lean one.
+// Whether the program has a udf test: it then needs a scan kernel instance
+// with the udf path.
 bool program_has_udf(const Query &q) {
   for (int i = 0; i < q.ninstr; ++i)
     if (q.code[i].op == OP_UDF) return true;
   return false;
 }
 
-// Consumer warps of the scan kernel instance a launch uses.
-int scan_consumers(bool udf) { return udf ? kConsumers : kConsumersLean; }
+uint32_t read_bytes_per_row(const Query &q) {
+  uint32_t b = 0;
+  for (int i = 0; i < q.nref; ++i) b += q.ref_w[i];
+  return b;
+}
+
+// The block shape a single sub-query's scan uses: the predicate's tuning
+// (validated when it was set), else the automatic one.
+int query_shape(const Query &q, const esc_tuning &tu) {
+  const bool udf = program_has_udf(q);
+  const uint32_t b = read_bytes_per_row(q);
+  const int s = scan_shape_for(tu.consumer_warps, tu.rows_per_pass, udf, b);
+  return s >= 0 ? s : auto_scan_shape(udf, b > kWideBytes);
+}
+
+// The block shape of a launch that scans several queries (a batch or one
+// of its waves): the automatic shape, with the udf path if any program has
+// a udf, for wide programs if they hold most of the launch's bytes.
+int launch_shape(const Query *qs, int n) {
+  bool udf = false;
+  uint64_t wide = 0, all = 0;
+  for (int i = 0; i < n; ++i) {
+    if (qs[i].is_const) continue;
+    udf = udf || program_has_udf(qs[i]);
+    const uint64_t w = (uint64_t)qs[i].nrows * read_bytes_per_row(qs[i]);
+    all += w;
+    if (read_bytes_per_row(qs[i]) > kWideBytes) wide += w;
+  }
+  return auto_scan_shape(udf, 2 * wide > all);
+}
 
 bool program_constant(const Query &q, uint32_t *value) {
   if (q.nref != 0) return false;
@@ -1681,18 +1744,15 @@ esc_status alloc_async(void **p, size_t bytes, cudaStream_t st) {
   return ESC_OK;
 }
 
-// udf: some program of the launch has a udf test (the udf instance runs it).
-esc_status launch_scan(const Launch &L, bool udf, cudaStream_t st) {
+// shape: the block shape (kScanShapes) of the instance that runs the launch.
+esc_status launch_scan(const Launch &L, int shape, cudaStream_t st) {
   DeviceState *d;
   esc_status s = device_state(&d);
   if (s != ESC_OK) return s;
   if (L.total_units == 0) return ESC_OK;
   const uint32_t cap = (uint32_t)(d->sms * d->blocks_per_sm);
   const uint32_t grid = std::min<uint32_t>(cap, L.total_units);
-  if (udf)
-    scan_kernel<kConsumers, true><<<grid, kThreads, smem_bytes(), st>>>(L);
-  else
-    scan_kernel<kConsumersLean, false><<<grid, kThreadsLean, smem_bytes(), st>>>(L);
+  launch_scan_shape(shape, grid, L, st);
   ESC_CK(cudaGetLastError());
   return ESC_OK;
 }
@@ -1790,7 +1850,7 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   if (program_constant(L.q0, &cval)) {
     s = launch_const(L, cval, st);
   } else {
-    s = launch_scan(L, program_has_udf(L.q0), st);
+    s = launch_scan(L, query_shape(L.q0, p->tuning), st);
     if (s == ESC_OK && mode == MODE_SELECT) s = launch_write(L, L.q0.nwunits, st);
   }
   if (s != ESC_OK) {
@@ -1954,7 +2014,7 @@ esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *
   const int nw = (int)wend.size();
   std::vector<uint32_t> cidx;
   std::vector<uint32_t> w_units((size_t)nw, 0), w_wunits((size_t)nw, 0);
-  std::vector<bool> w_udf((size_t)nw, false);
+  std::vector<int> w_shape((size_t)nw, 0);
   uint64_t zeroed = 0, other = 0;
   for (int w = 0, k0 = 0; w < nw; k0 = wend[w++]) {
     uint64_t units = 0, wunits = 0;
@@ -1969,11 +2029,11 @@ esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *
         zeroed += select_zeroed_bytes(q);
         other += select_other_bytes(q);
       }
-      if (!q.is_const && program_has_udf(q)) w_udf[w] = true;
       if (units >= (1ull << 31)) return fail(ESC_EINVAL, "esc_batch_prepare: too many work units in one batch");
     }
     w_units[w] = (uint32_t)units;
     w_wunits[w] = (uint32_t)wunits;
+    w_shape[w] = launch_shape(&qs[k0], wend[w] - k0);
   }
   esc_batch *b = new (std::nothrow) esc_batch;
   if (!b) return fail(ESC_ENOMEM, "esc_batch_prepare: out of host memory");
@@ -2021,7 +2081,7 @@ esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *
       op += select_other_bytes(q);
       init[i] = q.nwunits;                            // counted down by the write kernel
     } else {
-      init[i] = q.ntiles * (unsigned)scan_consumers(w_udf[w]);  // counted down by the scan kernel
+      init[i] = q.ntiles * (unsigned)kScanShapes[w_shape[w]].consumers;  // counted down by the scan kernel
     }
   }
   if ((uintptr_t)op > (uintptr_t)base + total) {
@@ -2058,7 +2118,7 @@ esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *
       L.nq = wend[w] - k0;
       L.total_units = w_units[w];
       L.hdr = reinterpret_cast<ScratchHdr *>(b->scratch + 256 * (size_t)w);
-      ls = launch_scan(L, w_udf[w], cs);
+      ls = launch_scan(L, w_shape[w], cs);
       if (ls == ESC_OK) ls = launch_write(L, w_wunits[w], cs);
     }
     e = cudaStreamEndCapture(cs, &b->graph);
@@ -2185,8 +2245,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   uint8_t *zp = z + 256 + 2 * cnt_bytes + left_bytes;
   uint8_t *op = z + zbytes;
   std::vector<unsigned int> init((size_t)n);
-  bool udf = false;
-  for (int i = 0; i < n; ++i) udf = udf || (!qs[i].is_const && program_has_udf(qs[i]));
+  const int shape = launch_shape(qs.data(), n);
   for (int i = 0; i < n; ++i) {
     qs[i].count = &counts[i];
     qs[i].done_ns = dev_done_ns ? &done[i] : nullptr;
@@ -2199,7 +2258,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
       op += select_other_bytes(qs[i]);
       init[i] = qs[i].nwunits;
     } else {
-      init[i] = qs[i].ntiles * (unsigned)scan_consumers(udf);
+      init[i] = qs[i].ntiles * (unsigned)kScanShapes[shape].consumers;
     }
   }
   uint32_t *dev_cidx = reinterpret_cast<uint32_t *>(base + sizeof(Query) * (size_t)n);
@@ -2220,7 +2279,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
   L.total_units = (uint32_t)units;
   L.hdr = reinterpret_cast<ScratchHdr *>(z);
   s = cidx.empty() ? ESC_OK : launch_const_batch(L.queries, dev_cidx, (uint32_t)cidx.size(), st);
-  if (s == ESC_OK) s = launch_scan(L, udf, st);
+  if (s == ESC_OK) s = launch_scan(L, shape, st);
   if (s == ESC_OK) s = launch_write(L, (uint32_t)wunits, st);
   if (s == ESC_OK) {
     e = cudaMemcpyAsync(dev_counts, counts, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
@@ -2388,19 +2447,8 @@ esc_status noalloc_device(NoAllocDevice **out) {
   NoAllocDevice &d = g_noalloc[dev];
   if (!d.ready) {
     ESC_CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumers, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes()));
-    ESC_CK(cudaFuncSetAttribute(scan_kernel<kConsumersLean, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes()));
-    ESC_CK(cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWriteSmem));
-    ESC_CK(cudaFuncSetAttribute(shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SharedSmem::total));
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, scan_kernel<kConsumers, true>, kThreads,
-                                                         smem_bytes()));
-    if (d.blocks_per_sm < 1) return fail(ESC_ECUDA, "scan kernel does not fit on an SM");
-    int lean = 0;
-    ESC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lean, scan_kernel<kConsumersLean, false>, kThreadsLean,
-                                                         smem_bytes()));
-    if (lean < d.blocks_per_sm) return fail(ESC_ECUDA, "scan kernel (no udf) does not fit on an SM");
+    esc_status cs = configure_kernels(&d.blocks_per_sm);
+    if (cs != ESC_OK) return cs;
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
@@ -2469,10 +2517,7 @@ extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred
     ESC_CK(cudaGetLastError());
   } else if (L.total_units > 0) {
     const uint32_t grid = std::min<uint32_t>((uint32_t)(d->sms * d->blocks_per_sm), L.total_units);
-    if (program_has_udf(q))
-      scan_kernel<kConsumers, true><<<grid, kThreads, smem_bytes(), st>>>(L);
-    else
-      scan_kernel<kConsumersLean, false><<<grid, kThreadsLean, smem_bytes(), st>>>(L);
+    launch_scan_shape(query_shape(q, p->tuning), grid, L, st);
     ESC_CK(cudaGetLastError());
     if (mode == MODE_SELECT) {
       write_kernel<<<q.nwunits, kWriteThreads, kWriteSmem, st>>>(L);

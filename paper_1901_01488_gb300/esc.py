@@ -38,7 +38,8 @@ class esc_column(ctypes.Structure):
 
 class esc_tuning(ctypes.Structure):
     _fields_ = [("max_tile_rows", ctypes.c_uint32), ("max_unit_kb", ctypes.c_uint32),
-                ("units_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("units_per_sm", ctypes.c_int32), ("consumer_warps", ctypes.c_uint16),
+                ("rows_per_pass", ctypes.c_uint16)]
 
 
 class esc_rows(ctypes.Structure):
@@ -164,19 +165,23 @@ def esc_predicate_explain(pred: int) -> str:
     return buf.value.decode()
 
 
-def esc_predicate_set_tuning(pred: int, tuning: Optional[Tuple[int, int, int]]) -> None:
-    """tuning = (max_tile_rows, max_unit_kb, units_per_sm) or None for the defaults."""
+def esc_predicate_set_tuning(pred: int, tuning: Optional[Tuple[int, ...]]) -> None:
+    """tuning = (max_tile_rows, max_unit_kb, units_per_sm[, consumer_warps,
+    rows_per_pass]) -- the block shape (0, 0), automatic, when left out -- or
+    None for the defaults."""
     if tuning is None:
         _check(_lib.esc_predicate_set_tuning(pred, None), "esc_predicate_set_tuning")
         return
-    t = esc_tuning(tuning[0], tuning[1], tuning[2], 0)
+    shape = tuple(tuning[3:5]) if len(tuning) >= 5 else (0, 0)
+    t = esc_tuning(tuning[0], tuning[1], tuning[2], shape[0], shape[1])
     _check(_lib.esc_predicate_set_tuning(pred, ctypes.byref(t)), "esc_predicate_set_tuning")
 
 
-def esc_predicate_get_tuning(pred: int) -> Tuple[int, int, int]:
+def esc_predicate_get_tuning(pred: int) -> Tuple[int, int, int, int, int]:
+    """(max_tile_rows, max_unit_kb, units_per_sm, consumer_warps, rows_per_pass)."""
     t = esc_tuning()
     _check(_lib.esc_predicate_get_tuning(pred, ctypes.byref(t)), "esc_predicate_get_tuning")
-    return t.max_tile_rows, t.max_unit_kb, t.units_per_sm
+    return t.max_tile_rows, t.max_unit_kb, t.units_per_sm, t.consumer_warps, t.rows_per_pass
 
 
 def _rows_struct(capacity: int, row_ids: Optional[torch.Tensor], proj: Sequence[torch.Tensor]):

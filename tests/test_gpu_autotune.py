@@ -9,22 +9,39 @@ from paper_1901_01488_gb300 import datagen
 pytestmark = pytest.mark.gpu
 
 
-def test_tuning_never_changes_results(esc_mod=None):
+def test_tuning_never_changes_results():
+    """Every block shape and tile/unit size gives the oracle's count, ordered
+    ids and projected values (single calls, count and materialising)."""
+    import numpy as np
+    import oracle
     from paper_1901_01488_gb300 import build
     build.build()
     from paper_1901_01488_gb300 import esc
+    from paper_1901_01488_gb300.autotune import SHAPES, SHAPES_UDF
     t = datagen.skewed_table(3_000_011, seed=60, device="cuda")
+    host = t.host()
     tbl = esc.Table.from_datagen(t)
-    for pt in datagen.skewed_predicates(200)[::25]:
-        p = esc.Predicate(tbl, pt.text, datagen.SKEWED_PROJECTION)
-        ref = esc.select(tbl, p)
-        for cand in ((2048, 16, 64), (4096, 128, 1), (32768, 4096, 8), (256, 16, 3)):
+    proj = datagen.SKEWED_PROJECTION
+    tiles = ((2048, 16, 64), (4096, 128, 1), (32768, 4096, 8), (256, 16, 3), (32768, 512, 8))
+    texts = [pt.text for pt in datagen.skewed_predicates(200)[::25]]
+    texts.append("udf(price, qty, 97) > 40 AND code7 IN (1, 2, 5)")
+    for text in texts:
+        p = esc.Predicate(tbl, text, proj)
+        ids, pv = oracle.select(text, host, proj)
+        shapes = SHAPES_UDF if "udf" in text else SHAPES
+        for k, shape in enumerate(shapes):
+            cand = tiles[k % len(tiles)] + shape
             esc.esc_predicate_set_tuning(p.handle, cand)
             assert esc.esc_predicate_get_tuning(p.handle) == cand
-            got = esc.select(tbl, p)
-            assert got[0] == ref[0] and torch.equal(got[1], ref[1])
-            for a, b in zip(got[2], ref[2]):
-                assert torch.equal(a, b)
+            assert esc.count(tbl, p) == len(ids), (text, cand)
+            n, got_ids, got_proj = esc.select(tbl, p)
+            assert n == len(ids), (text, cand)
+            assert np.array_equal(got_ids.cpu().numpy().view(np.uint32), ids), (text, cand)
+            for name, c in zip(proj, got_proj):
+                assert np.array_equal(c.cpu().numpy(), pv[name]), (text, cand, name)
+        if "udf" in text:
+            with pytest.raises(esc.EscError):
+                esc.esc_predicate_set_tuning(p.handle, (32768, 512, 8, 23, 8))
         with pytest.raises(esc.EscError):
             esc.esc_predicate_set_tuning(p.handle, (300, 512, 8))
 
@@ -37,7 +54,7 @@ def test_autotuner_caches_choices(tmp_path):
     preds = [esc.Predicate(tbl, p.text) for p in datagen.skewed_predicates(40, seed0=7000)]
     tuner = Autotuner(esc, str(tmp_path / "tune.json"), repeats=2)
     chosen = tuner.tune(tbl, preds[:12])
-    assert chosen and all(len(v) == 3 for v in chosen.values())
+    assert chosen and all(len(v) == 5 for v in chosen.values())
     cache = json.load(open(tmp_path / "tune.json"))
     assert set(cache) == set(chosen)
     k = class_key(tbl, preds[0], False)
