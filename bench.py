@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=20_000, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20_000.0, help="serve: highest arrival rate of the sweep (per s)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals per rate")
+    ap.add_argument("--max-wave-rows", type=int, default=1_200_000_000,
+                    help="serve: table rows one wave may scan (0: no cap)")
+    ap.add_argument("--rates", type=str, default="", help="serve: comma-separated arrival rates (default: a sweep)")
     ap.add_argument("--pairs", type=int, default=1_000_000, help="surrogate: (predicate, exact count) pairs")
     return ap.parse_args()
 
@@ -565,11 +568,13 @@ def run_serve(args):
         s["materialised"] = sum(1 for r in done if r.proj)
         return s
 
-    rates = [r for r in (2_500, 5_000, 10_000, 15_000, 20_000) if r <= args.rate] or [args.rate]
+    rates = ([int(float(x)) for x in args.rates.split(",")] if args.rates else
+             [r for r in (2_500, 5_000, 10_000, 15_000, 20_000) if r <= args.rate] or [args.rate])
+    cap = args.max_wave_rows or None
     levels = {}
     for rate in rates:
         n = int(min(nmax, max(2_000, rate * args.serve_seconds)))
-        srv = serve.Server(esc, etabs, mem_budget=16 << 30, max_batch=512, streams=4)
+        srv = serve.Server(esc, etabs, mem_budget=16 << 30, max_batch=512, streams=4, max_wave_rows=cap)
         srv.run(requests(rate, min(512, n)))                                   # warm-up
         batched = srv.run(requests(rate, n))
         plain = serve.PlainServer(esc, etabs, streams=4)
@@ -586,7 +591,9 @@ def run_serve(args):
            "value": levels[top]["continuous_batching"]["throughput_per_s"],
            "config": {"workload": "Poisson arrivals over tables " + str(list(sizes)) + "; every fourth request "
                                   "materialises (key, day, price) when it selects <= 1M rows; continuous batching "
-                                  "on 4 streams, admission by device memory; predicates compiled on 4 host threads",
+                                  "on 4 streams, admission by device memory and by rows scanned per wave; "
+                                  "predicates compiled on 4 host threads",
+                      "max_wave_rows": cap,
                       "rates_per_s": rates},
            "levels": levels,
            "p99_under_1ms_up_to_rate": max(under) if under else None}

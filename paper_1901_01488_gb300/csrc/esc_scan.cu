@@ -19,8 +19,8 @@
 //    group (one decode per instruction for the run), keeping the
 //    boolean evaluation stack as 8-bit masks in one 64-bit register;
 //  * counts: popc per lane, one atomic per warp and query;
-//  * ordered compaction, first pass: the selection bitmap (lane-major),
-//    staged per tile in shared memory and written with one bulk copy, and a
+//  * ordered compaction, first pass: the selection bitmap (lane-major, one
+//    byte per lane and group, a coalesced 32-byte store per warp) and a
 //    total per compaction unit of 65536 rows; second pass (write_kernel,
 //    one block per compaction unit): a decoupled look-back over the unit
 //    totals (Merrill & Garland, "Single-pass Parallel Prefix Scan with
@@ -92,16 +92,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
-// Shared -> global bulk copy (async proxy), tracked by bulk groups.
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit_wait_read() {
-  asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -539,11 +529,8 @@ __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned l
   }
 }
 
-// Compaction results of one tile (the selection bitmap, 32 B per group),
-// staged in shared memory and written with one bulk copy by the tile's last
-// consumer.
-constexpr size_t kResGroups = kMaxTileRows / kGroup;
-constexpr size_t kResBytes = kResGroups * 32;
+// Groups of a full tile at most.
+constexpr size_t kTileGroups = kMaxTileRows / kGroup;
 
 // Shared-memory layout of the scan kernel (offsets in bytes).
 struct SmemLayout {
@@ -552,10 +539,8 @@ struct SmemLayout {
   static constexpr size_t bars = qslot + (size_t)kStages * sizeof(Query);  // full[S] empty[S]
   static constexpr size_t meta = bars + 2 * kStages * 8;
   static constexpr size_t slotq = meta + kStages * sizeof(StageMeta);      // [S] int32
-  static constexpr size_t take = slotq + kStages * 4;                       // [S] u32 pair claims
-  static constexpr size_t resdone = take + kStages * 4;                     // [S] u32 warps done (compaction)
-  static constexpr size_t res = (resdone + kStages * 4 + 127) & ~(size_t)127;  // [S] compaction results
-  static constexpr size_t total = res + kStages * kResBytes;
+  static constexpr size_t take = slotq + kStages * 4;                       // [S] u32 run claims
+  static constexpr size_t total = take + kStages * 4;
 };
 
 // Checked build: everything the evaluation of a stage will index -- every
@@ -565,7 +550,7 @@ struct SmemLayout {
 // release build.
 __device__ __forceinline__ bool stage_in_bounds(const Query *Q, int ngroups, ScratchHdr *hdr, int lane) {
 #ifdef ESC_CHECKED
-  bool ok = ESC_INB(hdr, ngroups >= 0 && (uint32_t)ngroups <= Q->gmax && Q->gmax <= (uint32_t)kResGroups, 10, ngroups);
+  bool ok = ESC_INB(hdr, ngroups >= 0 && (uint32_t)ngroups <= Q->gmax && Q->gmax <= (uint32_t)kTileGroups, 10, ngroups);
   ok = ok && ESC_INB(hdr, Q->ninstr >= 0 && Q->ninstr <= kMaxInstr && Q->nref <= kMaxRef, 11, Q->ninstr);
   const uint64_t span = (uint64_t)ngroups * kGroup;
   for (int pc = lane; ok && pc < Q->ninstr; pc += 32) {
@@ -609,7 +594,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
   StageMeta *meta = reinterpret_cast<StageMeta *>(smem + SmemLayout::meta);
   int32_t *slotq = reinterpret_cast<int32_t *>(smem + SmemLayout::slotq);
   uint32_t *take = reinterpret_cast<uint32_t *>(smem + SmemLayout::take);
-  uint32_t *resdone = reinterpret_cast<uint32_t *>(smem + SmemLayout::resdone);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -620,7 +604,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], NC);
       slotq[s] = -1;
-      resdone[s] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -753,10 +736,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       acc_ptr = nullptr;
       acc_q = -1;
     }
-    if (end) {
-      if (lane == 0) bulk_wait_all();  // bulk stores this warp issued have completed
-      break;
-    }
+    if (end) break;
     const uint8_t *stage = stages + (size_t)s * kStageBytes;
     const uint32_t rows = mt.rows;
     const int ngroups = (int)((rows + kGroup - 1) / kGroup);
@@ -779,7 +759,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
       // interpreter); the per-group epilogue branches on the mode (uniform)
       const uint32_t nwords = (Q->nrows + 31u) / 32u;
       uint32_t *bm = Q->bitmap;
-      uint32_t *rbm = reinterpret_cast<uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
       for (int j = claim(); j < nruns; j = claim()) {
         // the run's groups; past the stage's last group, that group again
         // (evaluated, not counted)
@@ -812,9 +791,12 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
             }
             uacc += c;
             // selection bitmap, lane-major: byte l of the group's 32 bytes is
-            // lane l's mask (bit 2j+i: row 64*j + 2*l + i of the group); the
-            // write kernel counts a group's rows from its bytes
-            reinterpret_cast<uint8_t *>(rbm)[gs[i] * 32 + lane] = (uint8_t)m;
+            // lane l's mask (bit 2j+i: row 64*j + 2*l + i of the group), one
+            // coalesced 32-byte store per warp; the write kernel counts a
+            // group's rows from its bytes
+            const uint64_t gi = (uint64_t)mt.tile * Q->gmax + (uint32_t)gs[i];
+            if (ESC_INB(hdr, gi < (uint64_t)Q->ntiles * Q->gmax, 17, gi))
+              reinterpret_cast<uint8_t *>(Q->bitmap)[gi * 32 + lane] = (uint8_t)m;
             continue;
           }
           const uint32_t gidx = (r0 + (uint32_t)gs[i] * kGroup) / kGroup;
@@ -828,29 +810,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           const uint32_t wi = gidx * 8u + (uint32_t)lane;
           if (lane < 8 && wi < nwords) bm[wi] = word;
         }
-      }
-    }
-    if (mode == MODE_SELECT && mt.dead == 0) {
-      // the tile's last consumer writes its staged results with bulk copies
-      // and waits until they have read shared memory before releasing the stage
-      fence_proxy_async_smem();
-      __syncwarp();
-      uint32_t last = 0;
-      if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&resdone[s], 1u) == (uint32_t)NC - 1u ? 1u : 0u;
-        __threadfence_block();
-      }
-      if (__shfl_sync(FULL, last, 0)) {
-        if (lane == 0) {
-          resdone[s] = 0;
-          const uint32_t ng = (uint32_t)ngroups;
-          const uint32_t *rb = reinterpret_cast<const uint32_t *>(smem + SmemLayout::res + (size_t)s * kResBytes);
-          if (ESC_INB(hdr, ((uint64_t)mt.tile * Q->gmax + ng) <= (uint64_t)Q->ntiles * Q->gmax, 17, mt.tile))
-            bulk_store(Q->bitmap + (size_t)mt.tile * Q->gmax * 8u, rb, ng * 32u);
-          bulk_commit_wait_read();
-        }
-        __syncwarp();
       }
     }
     if (mode != MODE_SELECT) retire_tile(Q->tiles_left, Q->done_ns, lane);

@@ -4,8 +4,10 @@ Not in the paper (there, the optimizer issues one sub-query per table with
 a selection, Sec. 2); this is the serving pattern around it.  Requests
 (table, predicate) arrive over time.  A host loop keeps `streams` waves in
 flight: whenever a stream is free it admits every request that has arrived,
-up to `max_batch` and within the device-memory budget (each request reserves
-the scratch and output bytes its materialisation needs), compiles their
+up to `max_batch`, within the device-memory budget (each request reserves
+the scratch and output bytes its materialisation needs) and within
+`max_wave_rows` table rows scanned (a wave's requests complete together, so
+one long wave would hold back every short request in it), compiles their
 predicates and launches them: count requests on one table, when at least
 `shared_min` of them arrived together, share one pass over it
 (esc_selectivity_shared_async); the others run as one batch
@@ -21,7 +23,9 @@ sub-query call, launched when it arrives (round robin over the streams).
 """
 from __future__ import annotations
 
+import contextlib
 import dataclasses
+import gc
 import time
 from collections import deque
 from concurrent.futures import ThreadPoolExecutor
@@ -59,18 +63,29 @@ def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
 
 
 def admit(pending: Deque[Request], in_flight: int, budget: int, max_batch: int,
-          size: Callable[[Request], int]) -> Tuple[List[Request], int]:
+          size: Callable[[Request], int], work: Optional[Callable[[Request], int]] = None,
+          max_work: Optional[int] = None) -> Tuple[List[Request], int]:
     """The next wave: requests from the front of `pending`, in arrival order,
-    while the wave holds fewer than `max_batch` and its bytes fit the budget
-    beside those in flight.  A request larger than the whole budget runs
-    alone once nothing else is in flight.  Returns (wave, its bytes)."""
+    while the wave holds fewer than `max_batch`, its bytes fit the budget
+    beside those in flight, and (with `work`) its work -- the rows it scans --
+    stays within `max_work`.  A wave's requests all complete when the wave
+    does, so the work cap bounds the latency a long wave adds to its short
+    requests.  A request larger than the whole budget runs alone once
+    nothing else is in flight; one above the work cap runs in a wave of its
+    own.  Returns (wave, its bytes)."""
     batch: List[Request] = []
     nbytes = 0
+    nwork = 0
     while pending and len(batch) < max_batch:
         b = size(pending[0])
         alone = not batch and in_flight == 0
         if in_flight + nbytes + b > budget and not alone:
             break
+        if work is not None and max_work is not None:
+            wk = work(pending[0])
+            if batch and nwork + wk > max_work:
+                break
+            nwork += wk
         batch.append(pending.popleft())
         nbytes += b
     return batch, nbytes
@@ -91,7 +106,8 @@ def wave_groups(batch: Sequence[Request], shared_min: int) -> Tuple[List[List[Re
 
 class Server:
     def __init__(self, esc, tables, mem_budget: int = 8 << 30, max_batch: int = 512, streams: int = 2,
-                 device="cuda", shared_min: int = 8, compile_threads: int = 4):
+                 device="cuda", shared_min: int = 8, compile_threads: int = 4,
+                 max_wave_rows: Optional[int] = 1_200_000_000):
         self.esc = esc
         self.tables = tables
         self.budget = mem_budget
@@ -105,12 +121,20 @@ class Server:
         self.shared_min = shared_min      # count requests per table that share one pass
         self.shared_launches = 0
         self.compile_threads = compile_threads
+        self.max_wave_rows = max_wave_rows  # table rows a wave may scan (None: no cap)
+        # per wave: launch and completion times (server clock, s), requests,
+        # shared passes, table rows scanned, and how long the launch took on the host
+        self.wave_log: List[dict] = []
 
     def _compile(self, r: Request):
         return self.esc.Predicate(self.tables[r.table], r.text, tuple(r.proj))
 
     def run(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Request]:
         """Serves `requests` (arrival times relative to the start) and returns them completed."""
+        with no_gc_pauses():
+            return self._run(requests, clock)
+
+    def _run(self, requests: Sequence[Request], clock) -> List[Request]:
         esc = self.esc
         pending: Deque[Request] = deque()
         queue = deque(sorted(requests, key=lambda r: r.arrival))
@@ -129,6 +153,7 @@ class Server:
                 w = slots[k]
                 if w is not None and w["event"].query():
                     t_done = clock() - t0
+                    w["log"]["done"] = t_done
                     counts = w["counts"].tolist()
                     for r, c in zip(w["reqs"], counts):
                         r.count = int(c)
@@ -140,9 +165,13 @@ class Server:
                 if slots[k] is None and pending:
                     batch, nbytes = admit(pending, self.in_flight_bytes, self.budget, self.max_batch,
                                           lambda r: request_bytes(self.tables[r.table].nrows, r,
-                                                                  self.widths[r.table]))
+                                                                  self.widths[r.table]),
+                                          lambda r: self.tables[r.table].nrows, self.max_wave_rows)
                     if batch:
+                        t_l = clock() - t0
                         self._launch(batch, k, st, nbytes, slots)
+                        slots[k]["log"].update(launch=t_l, host_s=clock() - t0 - t_l, stream=k)
+                        self.wave_log.append(slots[k]["log"])
                         progressed = True
             if not progressed:
                 time.sleep(0)
@@ -188,7 +217,26 @@ class Server:
         self.in_flight_bytes += nbytes
         self.peak_bytes = max(self.peak_bytes, self.in_flight_bytes)
         self.waves += 1
-        slots[k] = {"reqs": batch, "counts": counts, "event": ev, "bytes": nbytes, "preds": preds}
+        log = {"requests": len(batch), "shared": len(groups),
+               "rows": sum(self.tables[r.table].nrows for r in batch)}
+        slots[k] = {"reqs": batch, "counts": counts, "event": ev, "bytes": nbytes, "preds": preds, "log": log}
+
+
+@contextlib.contextmanager
+def no_gc_pauses():
+    """Runs a serving loop with Python's cyclic garbage collector off (one
+    collection first, the previous setting restored after): a full
+    collection over the loop's many small objects stops the polling thread
+    for tens of milliseconds, and every request in flight waits that long.
+    Memory is reclaimed by reference counting meanwhile."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 5) -> np.ndarray:
@@ -216,6 +264,10 @@ class PlainServer:
         self.compile_threads = compile_threads
 
     def run(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Request]:
+        with no_gc_pauses():
+            return self._run(requests, clock)
+
+    def _run(self, requests: Sequence[Request], clock) -> List[Request]:
         esc = self.esc
         queue = deque(sorted(requests, key=lambda r: r.arrival))
         pool = ThreadPoolExecutor(self.compile_threads)

@@ -82,3 +82,45 @@ def test_admission_by_memory(esc):
     srv.run(reqs)
     assert srv.peak_bytes <= budget
     assert srv.waves >= 3          # the budget forced several waves
+
+
+def test_plain_server_and_wave_cap_match_oracle(esc):
+    """The one-call-per-request baseline, and continuous batching with a small
+    cap on the rows a wave may scan, both return the oracle's counts and
+    ordered rows; the cap splits the work into more waves."""
+    from paper_1901_01488_gb300 import serve
+    tabs, etabs = _tables(esc)
+    hosts = [t.host() for t in tabs]
+    work = datagen.batch_workload(160, seed=23, sizes=[t.nrows for t in tabs])
+    arr = serve.poisson_arrivals(len(work), 20_000, seed=4)
+    expect = {}
+
+    def requests():
+        out = []
+        for j, ((ti, p), a) in enumerate(zip(work, arr)):
+            proj = datagen.SKEWED_PROJECTION if j % 3 == 0 else ()
+            if j not in expect:
+                expect[j] = oracle.select(p.text, hosts[ti], tuple(proj)) if proj else \
+                    (oracle.count_parallel(p.text, hosts[ti], 8), None)
+            cap = len(expect[j][0]) + 1 if proj else 0
+            out.append(serve.Request(j, ti, p.text, float(a), proj, cap))
+        return out
+
+    def check(done):
+        for r in done:
+            if not r.proj:
+                assert r.count == expect[r.rid][0], r.text
+            else:
+                ids, pv = expect[r.rid]
+                n = len(ids)
+                assert r.count == n, r.text
+                assert np.array_equal(r.rows[1][:n].cpu().numpy().view(np.uint32), ids), r.text
+                for name, a in zip(r.proj, r.rows[2]):
+                    assert np.array_equal(a[:n].cpu().numpy(), pv[name]), (r.text, name)
+
+    check(serve.PlainServer(esc, etabs, streams=2).run(requests()))
+    wide = serve.Server(esc, etabs, mem_budget=1 << 30, max_batch=512, streams=2, max_wave_rows=None)
+    check(wide.run(requests()))
+    capped = serve.Server(esc, etabs, mem_budget=1 << 30, max_batch=512, streams=2, max_wave_rows=10_000_000)
+    check(capped.run(requests()))
+    assert capped.waves > wide.waves

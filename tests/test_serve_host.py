@@ -6,8 +6,8 @@ from collections import deque
 import numpy as np
 import pytest
 
-from paper_1901_01488_gb300.serve import (Request, admit, latency_summary, poisson_arrivals, request_bytes,
-                                          wave_groups)
+from paper_1901_01488_gb300.serve import (Request, admit, latency_summary, no_gc_pauses, poisson_arrivals,
+                                          request_bytes, wave_groups)
 
 
 def _reqs(spec):
@@ -33,6 +33,25 @@ def test_admission_in_order_within_budget_and_batch_size():
     assert batch == []
     batch, nbytes = admit(big, in_flight=0, budget=10, max_batch=10, size=lambda r: 50)
     assert [r.rid for r in batch] == [0] and nbytes == 50 and len(big) == 1
+
+
+def test_admission_work_cap():
+    pend = deque(_reqs([(0, False)] * 6))
+    rows = [100, 300, 50, 700, 10, 10]
+    w = lambda r: rows[r.rid]
+    size = lambda r: 1
+    batch, _ = admit(pend, 0, 1000, 10, size, w, 400)
+    assert [r.rid for r in batch] == [0, 1]                         # 100 + 300; + 50 > 400
+    batch, _ = admit(pend, 0, 1000, 10, size, w, 400)
+    assert [r.rid for r in batch] == [2]                            # 50 + 700 > 400
+    batch, _ = admit(pend, 0, 1000, 10, size, w, 400)
+    assert [r.rid for r in batch] == [3]                            # above the cap: a wave of its own
+    batch, _ = admit(pend, 0, 1000, 10, size, w, 400)
+    assert [r.rid for r in batch] == [4, 5] and not pend
+    # no cap: only the batch size and the budget
+    pend = deque(_reqs([(0, False)] * 6))
+    batch, _ = admit(pend, 0, 1000, 10, size, w, None)
+    assert len(batch) == 6
 
 
 def test_admission_never_exceeds_the_budget_when_requests_fit():
@@ -85,3 +104,18 @@ def test_poisson_arrivals_and_latency_summary():
     assert s["p50_ms"] == pytest.approx(5.05) and s["max_ms"] == pytest.approx(10.0)
     assert s["p99_ms"] == pytest.approx(np.percentile(np.arange(1, 101) * 0.1, 99))
     assert s["throughput_per_s"] == pytest.approx(100 / (reqs[-1].done - reqs[0].arrival))
+
+
+def test_no_gc_pauses_restores_the_setting():
+    import gc
+    assert gc.isenabled()
+    with no_gc_pauses():
+        assert not gc.isenabled()
+    assert gc.isenabled()
+    gc.disable()
+    try:
+        with no_gc_pauses():
+            assert not gc.isenabled()
+        assert not gc.isenabled()                 # left as it was
+    finally:
+        gc.enable()
