@@ -208,7 +208,7 @@ esc_status esc_selectivity_async(const esc_table *table, const esc_pred *pred,
  * `rows` (materialisation) the table may have up to about 95 million rows
  * (the scratch needs about nrows/8 bytes); larger tables give ESC_EINVAL.
  * The first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture.  Every call
+ * allocation).  Every call
  * shares the one array: calls whose GPU work overlaps (different streams,
  * or host threads without ordering) race and give wrong results.
  * Synchronises `stream`. */

@@ -529,8 +529,8 @@ __device__ __forceinline__ void retire_tile(unsigned int *tiles_left, unsigned l
   }
 }
 
-// Groups of a full tile at most.
-constexpr size_t kTileGroups = kMaxTileRows / kGroup;
+// Groups of a full tile at most (checked build).
+[[maybe_unused]] constexpr size_t kTileGroups = kMaxTileRows / kGroup;
 
 // Shared-memory layout of the scan kernel (offsets in bytes).
 struct SmemLayout {
