@@ -694,10 +694,10 @@ def run_surrogate(args):
     ntr, nva = int(0.8 * n), int(0.9 * n)
     model = S.Surrogate(esc, seed=3)
     xb, yb = S.to_bf16(X, "cuda"), torch.from_numpy(y).cuda()
-    epochs = 20
+    epochs = 60
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    curve = model.fit(xb[:ntr], yb[:ntr], epochs=epochs, batch=4096, lr=3e-3)
+    curve = model.fit(xb[:ntr], yb[:ntr], epochs=epochs, batch=4096, lr=3e-3, lr_end=1e-5)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     a.record(st)
@@ -726,7 +726,8 @@ def run_surrogate(args):
            "labels": {"wall_s": label_s, "per_s": n / label_s, "predicate_generation_s": gen_s,
                       "device_ms_per_65536": dev_ms, "device_labels_per_s": len(sl) / (dev_ms / 1e3),
                       "labels_by": "shared scans of 2048 predicates", "features_s": feat_s},
-           "training": {"epochs": epochs, "samples": ntr, "wall_s": train_s, "loss_first_last": [curve[0], curve[-1]],
+           "training": {"epochs": epochs, "step_size": "3e-3 to 1e-5, half cosine", "samples": ntr,
+                        "wall_s": train_s, "loss_first_last": [curve[0], curve[-1]],
                         "samples_per_s": ntr * epochs / train_s},
            "inference": {"samples": n - nva, "ms": pred_ms, "samples_per_s": (n - nva) / (pred_ms / 1e3),
                          "gflops": (n - nva) * flops_per_sample / (pred_ms / 1e3) / 1e9},

@@ -248,13 +248,17 @@ class Surrogate:
         return y
 
     def fit(self, x_bf16: torch.Tensor, y: torch.Tensor, epochs: int = 20, batch: int = 4096,
-            lr: float = 2e-3, seed: int = 1) -> List[float]:
-        """Minibatch Adam on mean squared error; returns the mean loss per epoch."""
+            lr: float = 2e-3, seed: int = 1, lr_end: Optional[float] = None) -> List[float]:
+        """Minibatch Adam on mean squared error; returns the mean loss per epoch.
+        With `lr_end` the step size falls from `lr` to `lr_end` along a half
+        cosine over the steps of the run (less noise in the final weights)."""
         n = x_bf16.shape[0]
         grad = torch.zeros_like(self.params)
         lsum = torch.zeros(1, dtype=torch.float32, device=self.device)
         gen = torch.Generator(device=self.device).manual_seed(seed)
         curve = []
+        steps = epochs * ((n + batch - 1) // batch)
+        k = 0
         for _ in range(epochs):
             perm = torch.randperm(n, device=self.device, generator=gen)
             lsum.zero_()
@@ -265,7 +269,11 @@ class Surrogate:
                 grad.zero_()
                 self.esc.esc_mlp_grad(xb, yb, self.wbf, self.params, grad, lsum)
                 self.step += 1
-                self.esc.esc_mlp_adam(self.params, self.wbf, grad, self.m, self.v, lr, self.step)
+                rate = lr
+                if lr_end is not None:
+                    rate = lr_end + (lr - lr_end) * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps - 1)))
+                k += 1
+                self.esc.esc_mlp_adam(self.params, self.wbf, grad, self.m, self.v, rate, self.step)
             curve.append(float(lsum.item()) / n)
         return curve
 

@@ -111,7 +111,7 @@ def test_training_gain_over_independence_and_fallback(esc):
     model = S.Surrogate(esc, seed=3)
     xb = S.to_bf16(X, "cuda")
     yb = torch.from_numpy(y.astype(np.float32)).cuda()
-    curve = model.fit(xb[:ntr], yb[:ntr], epochs=80, batch=2048, lr=1e-3)
+    curve = model.fit(xb[:ntr], yb[:ntr], epochs=80, batch=2048, lr=1e-3, lr_end=1e-5)
     assert curve[-1] < 0.5 * curve[0], curve
     est = 10.0 ** (base[nva:] + model.predict(xb[nva:]).cpu().numpy().astype(np.float64)) * t.nrows
     q = S.qerror(est, counts[nva:])
@@ -153,3 +153,20 @@ def test_checkpoint_resume(esc, tmp_path):
     ca = a.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=10)
     cb = b.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=10)
     assert np.allclose(ca, cb, rtol=1e-3), (ca, cb)
+
+
+def test_step_size_schedule(esc):
+    """The cosine schedule: one epoch at lr_end = lr trains exactly as the
+    constant step size does, and a run with lr_end gives finite weights."""
+    from paper_1901_01488_gb300 import surrogate as S
+    g = torch.Generator().manual_seed(5)
+    x = torch.randn(4096, 64, generator=g)
+    xb = S.to_bf16(x.numpy(), "cuda")
+    yb = torch.randn(4096, generator=g).cuda()
+    a, b = S.Surrogate(esc, seed=4), S.Surrogate(esc, seed=4)
+    ca = a.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11)
+    cb = b.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11, lr_end=1e-3)
+    assert ca == cb and torch.equal(a.params, b.params)
+    c = S.Surrogate(esc, seed=4)
+    c.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11, lr_end=1e-5)
+    assert bool(torch.isfinite(c.params).all()) and not torch.equal(c.params, a.params)
