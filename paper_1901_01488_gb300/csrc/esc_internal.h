@@ -146,7 +146,8 @@ struct ScratchHdr {
   unsigned int abort;    // set together with status; everyone stops working
   unsigned int site;     // checked build: where the first out-of-range index was found
   unsigned long long value;  // checked build: that index
-  unsigned long long pad;
+  unsigned int warps_done;   // consumer warps of the scan that have finished (see Launch::count_out)
+  unsigned int pad;
 };
 static_assert(sizeof(ScratchHdr) == 32, "ScratchHdr layout");
 

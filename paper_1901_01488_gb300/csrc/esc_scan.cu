@@ -513,7 +513,10 @@ struct Launch {
   int32_t nq;
   uint32_t total_units;  // work units (scan tickets) of all queries
   ScratchHdr *hdr;
-  uint32_t pad[4];
+  // single sub-query: where the scan's last consumer warp stores the final
+  // count (the caller's word, which then needs no zeroing); null: none
+  unsigned long long *count_out;
+  uint32_t pad[2];
   Query q0;
 };
 
@@ -818,6 +821,16 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
     if (++s == kStages) {
       s = 0;
       phase ^= 1u;
+    }
+  }
+  // Single sub-query: the last consumer warp of the grid to finish (every
+  // warp has flushed its count by now) stores the final count in the
+  // caller's word.
+  if (L.count_out && lane == 0) {
+    __threadfence();
+    if (atomicAdd(&hdr->warps_done, 1u) == gridDim.x * (uint32_t)NC - 1u) {
+      __threadfence();
+      *L.count_out = atomicAdd(L.q0.count, 0ull);
     }
   }
 }
@@ -1794,8 +1807,14 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   const size_t other = mode == MODE_SELECT ? select_other_bytes(L.q0) : 0;
   void *mem = nullptr;
   if ((s = alloc_async(&mem, head + zeroed + other, st)) != ESC_OK) return s;
+  // The caller's count word: a scan stores the final count there itself (the
+  // counting goes to the zeroed scratch); the constant kernel, and a launch
+  // without work, count into the word, which is then zeroed first.
+  uint32_t cval = 0;
+  const bool constant = program_constant(L.q0, &cval);
+  const bool direct = dev_count && !constant && L.total_units > 0;
   cudaError_t e = cudaMemsetAsync(mem, 0, head + zeroed, st);
-  if (e == cudaSuccess && dev_count) e = cudaMemsetAsync(dev_count, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess && dev_count && !direct) e = cudaMemsetAsync(dev_count, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, st);
     return fail(ESC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -1803,10 +1822,10 @@ esc_status run_single(const esc_table *t, const esc_pred *p, esc_rows *rows, int
   uint8_t *base = static_cast<uint8_t *>(mem);
   SingleScratch *sc = static_cast<SingleScratch *>(mem);
   L.hdr = &sc->hdr;
-  L.q0.count = dev_count ? dev_count : &sc->count;
+  L.q0.count = dev_count && !direct ? dev_count : &sc->count;
+  L.count_out = direct ? dev_count : nullptr;
   if (mode == MODE_SELECT) select_bind(L.q0, base + head, base + head + zeroed);
-  uint32_t cval = 0;
-  if (program_constant(L.q0, &cval)) {
+  if (constant) {
     s = launch_const(L, cval, st);
   } else {
     s = launch_scan(L, query_shape(L.q0, p->tuning), st);
