@@ -156,8 +156,9 @@ def test_checkpoint_resume(esc, tmp_path):
 
 
 def test_step_size_schedule(esc):
-    """The cosine schedule: one epoch at lr_end = lr trains exactly as the
-    constant step size does, and a run with lr_end gives finite weights."""
+    """The cosine schedule: with lr_end = lr it trains as the constant step
+    size does (up to the order of the gradient kernel's float atomics), and
+    a run with lr_end gives finite, different weights."""
     from paper_1901_01488_gb300 import surrogate as S
     g = torch.Generator().manual_seed(5)
     x = torch.randn(4096, 64, generator=g)
@@ -166,7 +167,8 @@ def test_step_size_schedule(esc):
     a, b = S.Surrogate(esc, seed=4), S.Surrogate(esc, seed=4)
     ca = a.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11)
     cb = b.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11, lr_end=1e-3)
-    assert ca == cb and torch.equal(a.params, b.params)
+    assert np.allclose(ca, cb, rtol=1e-4), (ca, cb)
+    assert torch.allclose(a.params, b.params, rtol=1e-3, atol=1e-5)
     c = S.Surrogate(esc, seed=4)
     c.fit(xb, yb, epochs=2, batch=512, lr=1e-3, seed=11, lr_end=1e-5)
-    assert bool(torch.isfinite(c.params).all()) and not torch.equal(c.params, a.params)
+    assert bool(torch.isfinite(c.params).all()) and not torch.allclose(c.params, a.params, rtol=1e-3, atol=1e-5)
