@@ -14,6 +14,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import os
 import statistics
@@ -134,6 +135,23 @@ class Clocks:
                 "samples": len(sm)}
 
 
+@contextlib.contextmanager
+def nvtx(name: str):
+    """An NVTX range around a bench phase, for timeline tools (nothing where
+    torch was built without NVTX)."""
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+        pushed = True
+    except Exception:
+        pushed = False
+    try:
+        yield
+    finally:
+        if pushed:
+            torch.cuda.nvtx.range_pop()
+
+
 def pred_bytes_per_row(pred) -> int:
     return sum(WIDTH[t] for _, t in pred_refs(pred))
 
@@ -235,7 +253,7 @@ def run_esc(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
+    with Clocks(local) as clk, nvtx("timed select steps"):
         t_start.record(stream)
         for k in range(K):
             step(k)
@@ -279,20 +297,21 @@ def run_esc(args):
 
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e_start.record(stream)
-    copy_st.wait_event(e_start)
-    h2d_into(0)
-    for s_ in range(args.e2e_steps):
-        k = s_ % 2
-        stream.wait_event(copied[k])
-        if s_ + 1 < args.e2e_steps:
-            h2d_into(1 - k)
-        for j, p in enumerate(tpreds[k]):
-            esc.esc_selectivity_async(tabs[k].handle, p.handle, dev_counts[j:j + 1], rows, stream)
-        used[k].record(stream)
-        host_counts.copy_(dev_counts, non_blocking=True)
-    e_end.record(stream)
-    torch.cuda.synchronize()
+    with nvtx("end-to-end steps"):
+        e_start.record(stream)
+        copy_st.wait_event(e_start)
+        h2d_into(0)
+        for s_ in range(args.e2e_steps):
+            k = s_ % 2
+            stream.wait_event(copied[k])
+            if s_ + 1 < args.e2e_steps:
+                h2d_into(1 - k)
+            for j, p in enumerate(tpreds[k]):
+                esc.esc_selectivity_async(tabs[k].handle, p.handle, dev_counts[j:j + 1], rows, stream)
+            used[k].record(stream)
+            host_counts.copy_(dev_counts, non_blocking=True)
+        e_end.record(stream)
+        torch.cuda.synchronize()
     e_ms = e_start.elapsed_time(e_end) / args.e2e_steps
     assert host_counts.tolist() == counts
     e2e_value = args.rows * len(preds) * world / (e_ms / 1e3)
@@ -301,12 +320,13 @@ def run_esc(args):
     # only), CUDA events around each call on its stream, after the timed region
     scan_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in preds]
     for rep_ in range(2):
-        for j, p in enumerate(preds):
-            if rep_ == 1:
-                scan_ev[j][0].record(stream)
-            esc.esc_selectivity_async(table.handle, p.handle, dev_counts[j:j + 1], None, stream)
-            if rep_ == 1:
-                scan_ev[j][1].record(stream)
+        with nvtx("count calls (roofline)" if rep_ == 1 else "count calls (warm-up)"):
+            for j, p in enumerate(preds):
+                if rep_ == 1:
+                    scan_ev[j][0].record(stream)
+                esc.esc_selectivity_async(table.handle, p.handle, dev_counts[j:j + 1], None, stream)
+                if rep_ == 1:
+                    scan_ev[j][1].record(stream)
     torch.cuda.synchronize()
     assert dev_counts.tolist() == counts
     scan_s = sum(a.elapsed_time(b) for a, b in scan_ev) / 1e3

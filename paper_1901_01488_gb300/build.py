@@ -81,7 +81,7 @@ def _build_locked(force: bool, verbose_ptxas: bool) -> str:
     for lib, lib_objs in ((LIB, objs[:n]), (LIB_CHECKED, objs[n:])):
         if force or _stale(lib, lib_objs):
             tmp = lib + f".tmp{os.getpid()}"
-            cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *lib_objs]
+            cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *lib_objs, "-ldl"]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

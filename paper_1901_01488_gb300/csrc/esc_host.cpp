@@ -896,6 +896,7 @@ uint64_t esc_table_nrows(const esc_table *t) { return t ? t->nrows : 0; }
 
 esc_status esc_predicate_compile(const esc_table *t, const char *text, const char *const *proj,
                                  int32_t nproj, esc_pred **out) {
+  ESC_RANGE("esc_predicate_compile");
   if (!out) return fail(ESC_EINVAL, "esc_predicate_compile: out is NULL");
   *out = nullptr;
   if (!t || !text) return fail(ESC_EINVAL, "esc_predicate_compile: table and text are required");
@@ -976,6 +977,7 @@ esc_status esc_predicate_destroy(esc_pred *p) {
 
 esc_status esc_predicate_compile_many(const esc_table *t, const char *const *texts, int32_t n,
                                       const char *const *proj, int32_t nproj, esc_pred **out, int32_t nthreads) {
+  ESC_RANGE("esc_predicate_compile_many");
   if (n < 0 || (n > 0 && (!texts || !out)))
     return fail(ESC_EINVAL, "esc_predicate_compile_many: bad arguments");
   for (int32_t i = 0; i < n; ++i) out[i] = nullptr;

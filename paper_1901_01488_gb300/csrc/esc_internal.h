@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/esc.h"
+#include <nvtx3/nvToolsExt.h>
 
 #ifdef __CUDACC__
 #define ESC_HD __host__ __device__
@@ -207,6 +208,16 @@ esc_status device_status(const ScratchHdr &h, const char *where);
 // Test hook: true when a device allocation of the library is to fail
 // (esc_debug_fail_allocs counts them down).
 bool inject_alloc_failure();
+// A named range on the calling host thread for timeline tools (NVTX; with
+// no tool attached a push or pop is a call through a no-op pointer).  Every
+// public entry point that launches GPU work opens one.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define ESC_RANGE(name) ::esc::NvtxRange esc_nvtx_range_(name)
 // Defaults of esc_tuning.
 constexpr esc_tuning kDefaultTuning{32768u, 512u, 8, 0, 0};
 // Fills the static part of a Query (program, read columns, projection) for a pred.

@@ -239,6 +239,7 @@ extern "C" {
 
 esc_status esc_mlp_forward(const uint16_t *x_bf16, uint64_t batch, const uint16_t *w_bf16, const float *params,
                            float *y, void *stream) {
+  ESC_RANGE("esc_mlp_forward");
   if (batch == 0) return ESC_OK;
   if (!x_bf16 || !w_bf16 || !params || !y) return fail(ESC_EINVAL, "esc_mlp_forward: NULL argument");
   ESC_MLP_CK(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem()));
@@ -251,6 +252,7 @@ esc_status esc_mlp_forward(const uint16_t *x_bf16, uint64_t batch, const uint16_
 
 esc_status esc_mlp_grad(const uint16_t *x_bf16, const float *target, uint64_t batch, const uint16_t *w_bf16,
                         const float *params, float *grad, float *loss_sum, void *stream) {
+  ESC_RANGE("esc_mlp_grad");
   if (batch == 0) return ESC_OK;
   if (!x_bf16 || !target || !w_bf16 || !params || !grad || !loss_sum)
     return fail(ESC_EINVAL, "esc_mlp_grad: NULL argument");
@@ -264,6 +266,7 @@ esc_status esc_mlp_grad(const uint16_t *x_bf16, const float *target, uint64_t ba
 
 esc_status esc_mlp_adam(float *params, uint16_t *w_bf16, const float *grad, float *m, float *v, uint64_t n, float lr,
                         float beta1, float beta2, float eps, int32_t step, void *stream) {
+  ESC_RANGE("esc_mlp_adam");
   if (!params || !w_bf16 || !grad || !m || !v || step < 1) return fail(ESC_EINVAL, "esc_mlp_adam: bad argument");
   const float bc1 = 1.0f - powf(beta1, (float)step);
   const float bc2 = 1.0f - powf(beta2, (float)step);

@@ -1859,6 +1859,7 @@ esc_status finish_single(SingleScratch *sc, uint64_t *count, cudaStream_t st) {
 extern "C" {
 
 esc_status esc_selectivity(const esc_table *t, const esc_pred *p, uint64_t *count, esc_rows *rows, void *stream) {
+  ESC_RANGE("esc_selectivity");
   if (!count) return fail(ESC_EINVAL, "esc_selectivity: count is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SingleScratch *sc = nullptr;
@@ -1877,6 +1878,7 @@ esc_status esc_selectivity(const esc_table *t, const esc_pred *p, uint64_t *coun
 
 esc_status esc_selectivity_async(const esc_table *t, const esc_pred *p, uint64_t *dev_count, esc_rows *rows,
                                  void *stream) {
+  ESC_RANGE("esc_selectivity_async");
   if (!dev_count) return fail(ESC_EINVAL, "esc_selectivity_async: dev_count is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SingleScratch *sc = nullptr;
@@ -1891,6 +1893,7 @@ esc_status esc_selectivity_async(const esc_table *t, const esc_pred *p, uint64_t
 
 esc_status esc_bitmap_build(const esc_table *dim, const esc_pred *p, uint32_t *dev_bitmap, uint64_t *count,
                             void *stream) {
+  ESC_RANGE("esc_bitmap_build");
   if (!dim) return fail(ESC_EINVAL, "esc_bitmap_build: dim is NULL");
   if (!dev_bitmap && dim->nrows > 0) return fail(ESC_EINVAL, "esc_bitmap_build: dev_bitmap is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -2125,10 +2128,12 @@ esc_status esc_batch_prepare(const esc_table *const *tables, const esc_pred *con
 
 esc_status esc_batch_prepare_waves(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
                                    const esc_rows *rows, int32_t waves, esc_batch **out) {
+  ESC_RANGE("esc_batch_prepare_waves");
   return batch_prepare(tables, preds, n, rows, waves, out);
 }
 
 esc_status esc_batch_run(esc_batch *b, uint64_t *dev_counts, uint64_t *dev_done_ns, void *stream) {
+  ESC_RANGE("esc_batch_run");
   if (!b) return fail(ESC_EINVAL, "esc_batch_run: batch is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ESC_CK(cudaGraphLaunch(b->exec, st));
@@ -2183,6 +2188,7 @@ esc_status esc_selectivity_batch(const esc_table *const *tables, const esc_pred 
 esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc_pred *const *preds, int32_t n,
                                        const esc_rows *rows, uint64_t *dev_counts, uint64_t *dev_done_ns,
                                        void *stream) {
+  ESC_RANGE("esc_selectivity_batch_async");
   if (n < 1 || !tables || !preds || !dev_counts)
     return fail(ESC_EINVAL, "esc_selectivity_batch_async: need n >= 1 tables, predicates and dev_counts");
   std::vector<Query> qs((size_t)n);
@@ -2330,6 +2336,7 @@ static esc_status run_shared_group(const esc_table *t, const esc_pred *const *pr
 
 esc_status esc_selectivity_shared_async(const esc_table *t, const esc_pred *const *preds, int32_t n,
                                         uint64_t *dev_counts, void *stream) {
+  ESC_RANGE("esc_selectivity_shared_async");
   if (!t || !preds || n < 1 || !dev_counts)
     return fail(ESC_EINVAL, "esc_selectivity_shared_async: need a table, n >= 1 predicates and dev_counts");
   for (int i = 0; i < n; ++i)
@@ -2442,6 +2449,7 @@ esc_status noalloc_device(NoAllocDevice **out) {
 
 extern "C" esc_status esc_selectivity_noalloc(const esc_table *t, const esc_pred *p, uint64_t *count,
                                               esc_rows *rows, void *stream) {
+  ESC_RANGE("esc_selectivity_noalloc");
   if (!count) return fail(ESC_EINVAL, "esc_selectivity_noalloc: count is NULL");
   if (!t || !p) return fail(ESC_EINVAL, "esc_selectivity_noalloc: table and predicate are required");
   if (p->table != t) return fail(ESC_EINVAL, "esc_selectivity_noalloc: predicate was compiled against another table");

@@ -222,6 +222,7 @@ using namespace esc;
 extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *const *fk_cols, int32_t ndims,
                                           const uint32_t *const *dev_bitmaps, const uint64_t *dim_rows,
                                           uint64_t *subset_counts, void *stream) {
+  ESC_RANGE("esc_semijoin_counts");
   if (!fact || !fk_cols || !dev_bitmaps || !dim_rows || !subset_counts)
     return fail(ESC_EINVAL, "esc_semijoin_counts: NULL argument");
   if (ndims < 1 || ndims > kSjMaxDims) return fail(ESC_EINVAL, "esc_semijoin_counts: ndims must be 1..4");
