@@ -7,13 +7,14 @@
 // and on the host, for every dimension subset S,
 //   count(S) = sum over v that contain S of h[v]   (superset sum).
 //
-// Kernel shape: persistent grid of 2 blocks of 512 threads per SM (shared
+// Kernel shape: persistent grid of one block of 512 threads per SM (shared
 // memory sized to the bitmaps it holds, the rest of the SM's on-chip memory
-// left to L1); each thread streams 8 rows per step with 16-byte
-// non-allocating loads of every FK column (4 rows per load).  The kernel is specialised on how many bitmaps
-// sit in shared memory (dimensions are ordered smallest bitmap first, so the
-// shared ones come first): each probe is then a fixed sequence -- clamp the
-// word index, load, shift, mask with the bounds test.  The 16 bins are 8-bit
+// left to L1; up to 128 registers a thread); each thread streams 8 rows per
+// step with 16-byte non-allocating loads of every FK column (4 rows per
+// load).  The kernel is specialised on how many bitmaps sit in shared memory
+// (dimensions are ordered smallest bitmap first, so the shared ones come
+// first): each probe is then a fixed sequence -- clamp the word index, load,
+// shift, mask with the bounds test.  The 16 bins are 8-bit
 // counters in two 64-bit registers, added into shared per-block bins (warp
 // reductions) before they can overflow.
 #include <cuda_runtime.h>
@@ -29,7 +30,7 @@ namespace esc {
 
 constexpr int kSjThreads = 512;
 constexpr int kSjMaxDims = 4;
-constexpr uint32_t kSjSmemBitmapBytes = 96 * 1024;  // two blocks per SM
+constexpr uint32_t kSjSmemBitmapBytes = 96 * 1024;  // shared copies of the smaller bitmaps
 
 struct SjParams {
   const int32_t *fk[kSjMaxDims];       // in probe order
@@ -108,7 +109,7 @@ __device__ __forceinline__ uint32_t probe_row(const SjParams &P, const uint32_t 
 }
 
 template <int ND, int NS>
-__global__ void __launch_bounds__(kSjThreads, 2) semijoin_kernel(const __grid_constant__ SjParams P) {
+__global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_constant__ SjParams P) {
   extern __shared__ __align__(16) uint32_t sbm[];
   __shared__ unsigned int bins[16];
 #pragma unroll
@@ -279,7 +280,7 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
   const size_t smem = (size_t)std::max<uint32_t>(smem_words, 4) * 4;
   P.smem_words = (uint32_t)(smem / 4);
   const uint32_t chunks = P.nrows / 8u;
-  const int grid = std::max(1, std::min<int>(sms * 2, (int)((chunks + kSjThreads - 1) / kSjThreads)));
+  const int grid = std::max(1, std::min<int>(sms, (int)((chunks + kSjThreads - 1) / kSjThreads)));
   if (e == cudaSuccess) {
     switch (ndims) {
       case 1: e = launch_nd<1>(P, ns, smem, grid, st); break;
