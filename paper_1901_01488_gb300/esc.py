@@ -172,7 +172,9 @@ def esc_predicate_set_tuning(pred: int, tuning: Optional[Tuple[int, ...]]) -> No
     if tuning is None:
         _check(_lib.esc_predicate_set_tuning(pred, None), "esc_predicate_set_tuning")
         return
-    shape = tuple(tuning[3:5]) if len(tuning) >= 5 else (0, 0)
+    if len(tuning) not in (3, 5):
+        raise ValueError("tuning is (max_tile_rows, max_unit_kb, units_per_sm[, consumer_warps, rows_per_pass])")
+    shape = tuple(tuning[3:5]) if len(tuning) == 5 else (0, 0)
     t = esc_tuning(tuning[0], tuning[1], tuning[2], shape[0], shape[1])
     _check(_lib.esc_predicate_set_tuning(pred, ctypes.byref(t)), "esc_predicate_set_tuning")
 

@@ -43,6 +43,8 @@ def test_tuning_ranges_and_defaults(esc):
         with pytest.raises(esc.EscError):
             esc.esc_predicate_set_tuning(p.handle, bad)
         assert esc.esc_predicate_get_tuning(p.handle) == (8192, 128, 16, 0, 0)    # unchanged
+    with pytest.raises(ValueError):
+        esc.esc_predicate_set_tuning(p.handle, (8192, 512, 8, 19))            # a shape needs both numbers
     esc.esc_predicate_set_tuning(p.handle, None)
     assert esc.esc_predicate_get_tuning(p.handle) == autotune.DEFAULT
     for tile in autotune.TILE_CANDIDATES:                                  # every candidate is valid
