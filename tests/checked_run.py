@@ -120,6 +120,18 @@ def main():
     got = esc.esc_semijoin_counts(fact.handle, ["fk"], [bm[:words]], [70_001])
     want = oracle.semijoin_counts([fk], [mark], [0, 1])
     assert got[1] == want[1] and got[0] == want[0] == len(fk), (got, want)
+    # a dimension too large for one block's shared memory: split over a pair of CTAs
+    big = 1_000_003
+    bw = rng.integers(0, 2**32, (big + 31) // 32, dtype=np.uint64).astype(np.uint32)
+    bmark = np.unpackbits(bw.view(np.uint8), bitorder="little")[:big].astype(np.uint8)
+    fk2 = rng.integers(-3, big + 4, 500_003).astype(np.int32)
+    fk2[:4] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, -1, big]
+    fact2 = esc.Table([("fk", "i32", torch.from_numpy(fk2).cuda()), ("fk2", "i32", torch.from_numpy(fk).cuda())],
+                      len(fk))
+    got = esc.esc_semijoin_counts(fact2.handle, ["fk", "fk2"], [torch.from_numpy(bw.view(np.int32).copy()).cuda(),
+                                                               bm[:words]], [big, 70_001])
+    want = oracle.semijoin_counts([fk2, fk], [bmark, mark], [0, 1, 2, 3])
+    assert got == [want[s] for s in range(4)], (got, want)
     torch.cuda.synchronize()
     print("ok")
 
