@@ -31,18 +31,13 @@ namespace esc {
 constexpr int kSjThreads = 512;
 constexpr int kSjMaxDims = 4;
 constexpr uint32_t kSjSmemBitmapBytes = 96 * 1024;  // shared copies of the smaller bitmaps
-// With the next bitmap split over a pair of CTAs (a cluster of two): the
-// shared copies plus this CTA's part.
-constexpr uint32_t kSjSplitSmemBytes = 200 * 1024;
 
 struct SjParams {
   const int32_t *fk[kSjMaxDims];       // in probe order
   const uint32_t *bitmap[kSjMaxDims];
   uint32_t dim_rows[kSjMaxDims];
-  uint32_t smem_off[kSjMaxDims];       // word offset in shared memory (the first NS dimensions, and
-                                       // the split one: its part in each CTA of the pair)
+  uint32_t smem_off[kSjMaxDims];       // word offset in shared memory (the first NS dimensions)
   uint32_t words[kSjMaxDims];
-  uint32_t split_half;                 // split dimension: words each CTA of the pair holds
   int32_t ndims;
   uint32_t nrows;
   unsigned long long *hist;            // 16 bins, zeroed
@@ -79,34 +74,6 @@ __device__ __forceinline__ uint32_t test_bit_checked(const uint32_t *bm, uint32_
   return test_bit(bm, key, rows, wlast, shared);
 }
 
-// Bit `key` of the bitmap split over the two CTAs of a cluster: CTA r holds
-// words [r*H, r*H + H) (H = split_half; past the last word, and in the zero
-// word at index `words`, zeros), so clamping the word index to `words` is the
-// whole bounds test, as for a shared copy.  The word is read from the owning
-// CTA's shared memory (distributed shared memory).
-__device__ __forceinline__ uint32_t test_bit_split(const uint32_t *part, uint32_t key, uint32_t words, uint32_t half,
-                                                   ScratchHdr *hdr) {
-  const uint32_t wi = min(key >> 5, words);
-  const uint32_t owner = wi >= half ? 1u : 0u;
-  const uint32_t local = wi - owner * half;
-  if (!ESC_INB(hdr, local < half, 33, wi)) return 0u;
-  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(part + local);
-  uint32_t raddr, w;
-  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(addr), "r"(owner));
-  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(w) : "r"(raddr) : "memory");
-  return (w >> (key & 31u)) & 1u;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
 __device__ __forceinline__ void bump(uint64_t &lo, uint64_t &hi, uint32_t m) {
   const uint64_t inc = 1ull << (8u * (m & 7u));
   if (m & 8u) hi += inc; else lo += inc;
@@ -126,16 +93,12 @@ __device__ __forceinline__ void flush(uint64_t &lo, uint64_t &hi, unsigned int *
   lo = hi = 0;
 }
 
-template <int ND, int NS, bool SPLIT>
+template <int ND, int NS>
 __device__ __forceinline__ uint32_t probe_row(const SjParams &P, const uint32_t *const (&bm)[ND],
                                               const uint32_t (&wmax)[ND], const int32_t (&k)[ND]) {
   uint32_t m = 0;
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    if (SPLIT && d == NS) {
-      m |= test_bit_split(bm[d], (uint32_t)k[d], P.words[d], P.split_half, P.hdr) << d;
-      continue;
-    }
 #ifdef ESC_CHECKED
     m |= test_bit_checked(bm[d], (uint32_t)k[d], P.dim_rows[d], wmax[d], d < NS, P.words[d], P.hdr) << d;
 #else
@@ -145,24 +108,10 @@ __device__ __forceinline__ uint32_t probe_row(const SjParams &P, const uint32_t 
   return m;
 }
 
-// SPLIT: launched in clusters of two CTAs; dimension NS (the next bitmap,
-// too large for one CTA's shared memory) is split over the pair's shared
-// memory and probed through distributed shared memory.
-template <int ND, int NS, bool SPLIT>
+template <int ND, int NS>
 __global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_constant__ SjParams P) {
   extern __shared__ __align__(16) uint32_t sbm[];
   __shared__ unsigned int bins[16];
-  if constexpr (SPLIT && NS < ND) {
-    // this CTA's part: words [r*H, r*H + H) of the bitmap, zeros past its end
-    const uint32_t H = P.split_half, r = cluster_rank();
-    const uint32_t tail = P.dim_rows[NS] & 31u;
-    for (uint32_t w = threadIdx.x; w < H; w += blockDim.x) {
-      const uint32_t g = r * H + w;
-      uint32_t x = g < P.words[NS] ? P.bitmap[NS][g] : 0u;
-      if (g + 1 == P.words[NS] && tail) x &= (1u << tail) - 1u;
-      if (ESC_INB(P.hdr, P.smem_off[NS] + w < P.smem_words, 31, P.smem_off[NS] + w)) sbm[P.smem_off[NS] + w] = x;
-    }
-  }
 #pragma unroll
   for (int d = 0; d < NS; ++d) {
     // the words (bits past the last row cleared) and a zero word
@@ -175,13 +124,11 @@ __global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_co
   }
   if (threadIdx.x < 16) bins[threadIdx.x] = 0;
   __syncthreads();
-  if constexpr (SPLIT) cluster_sync_all();  // both parts of the split bitmap are in place
   const uint32_t *bm[ND];
   uint32_t wmax[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const bool in_smem = d < NS || (SPLIT && d == NS);
-    bm[d] = in_smem ? sbm + P.smem_off[d] : P.bitmap[d];
+    bm[d] = d < NS ? sbm + P.smem_off[d] : P.bitmap[d];
     wmax[d] = d < NS ? P.words[d] : P.words[d] - 1u;  // shared: the zero word; global: words >= 1
   }
 
@@ -208,10 +155,10 @@ __global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_co
         k2[d] = v[d][q].z;
         k3[d] = v[d][q].w;
       }
-      bump(lo, hi, probe_row<ND, NS, SPLIT>(P, bm, wmax, k0));
-      bump(lo, hi, probe_row<ND, NS, SPLIT>(P, bm, wmax, k1));
-      bump(lo, hi, probe_row<ND, NS, SPLIT>(P, bm, wmax, k2));
-      bump(lo, hi, probe_row<ND, NS, SPLIT>(P, bm, wmax, k3));
+      bump(lo, hi, probe_row<ND, NS>(P, bm, wmax, k0));
+      bump(lo, hi, probe_row<ND, NS>(P, bm, wmax, k1));
+      bump(lo, hi, probe_row<ND, NS>(P, bm, wmax, k2));
+      bump(lo, hi, probe_row<ND, NS>(P, bm, wmax, k3));
     }
     }
     pending += 8;
@@ -227,87 +174,43 @@ __global__ void __launch_bounds__(kSjThreads, 1) semijoin_kernel(const __grid_co
       int32_t k[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) k[d] = P.fk[d][r];
-      bump(lo, hi, probe_row<ND, NS, SPLIT>(P, bm, wmax, k));
+      bump(lo, hi, probe_row<ND, NS>(P, bm, wmax, k));
     }
   }
   flush(lo, hi, bins);
   __syncthreads();
   if (threadIdx.x < 16 && bins[threadIdx.x]) atomicAdd(&P.hist[threadIdx.x], (unsigned long long)bins[threadIdx.x]);
-  // the pair's other CTA may still read this CTA's part of the split bitmap
-  if constexpr (SPLIT) {
-    __syncthreads();
-    cluster_sync_all();
-  }
 }
 
-template <int ND, int NS, bool SPLIT>
+template <int ND, int NS>
 cudaError_t launch_semijoin(const SjParams &P, size_t smem, int grid, cudaStream_t st) {
   static std::once_flag once[64];
   static cudaError_t attr[64];
-  static int max_clusters[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  auto fn = semijoin_kernel<ND, NS, SPLIT>;
   std::call_once(once[dev & 63], [&] {
-    attr[dev & 63] = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(SPLIT ? kSjSplitSmemBytes : kSjSmemBitmapBytes));
-    // without a split: as much L1 as the launch leaves, so that a bitmap
-    // probed in place (too large for shared memory) is mostly served from L1
-    // (its hot words: Zipf keys); with one: the shared memory the parts need
+    attr[dev & 63] = cudaFuncSetAttribute(semijoin_kernel<ND, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSjSmemBitmapBytes);
+    // as much L1 as the launch leaves: a bitmap probed in place (too large for
+    // shared memory) is then mostly served from L1 (its hot words: Zipf keys)
     if (attr[dev & 63] == cudaSuccess)
-      attr[dev & 63] = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                            (int)(SPLIT ? cudaSharedmemCarveoutMaxShared : cudaSharedmemCarveoutMaxL1));
-    if (SPLIT && attr[dev & 63] == cudaSuccess) {
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 2;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(2);
-      cfg.blockDim = dim3(kSjThreads);
-      cfg.dynamicSmemBytes = kSjSplitSmemBytes;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      attr[dev & 63] = cudaOccupancyMaxActiveClusters(&max_clusters[dev & 63], fn, &cfg);
-    }
+      attr[dev & 63] = cudaFuncSetAttribute(semijoin_kernel<ND, NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxL1);
   });
   if (attr[dev & 63] != cudaSuccess) return attr[dev & 63];
-  if (!SPLIT) {
-    fn<<<grid, kSjThreads, smem, st>>>(P);
-    return cudaGetLastError();
-  }
-  // clusters of two CTAs, no more pairs than can be resident at once
-  const int pairs = std::max(1, std::min((grid + 1) / 2, std::max(1, max_clusters[dev & 63])));
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(2 * pairs);
-  cfg.blockDim = dim3(kSjThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fn, P);
-}
-
-template <int ND, bool SPLIT>
-cudaError_t launch_nd(const SjParams &P, int ns, size_t smem, int grid, cudaStream_t st) {
-  switch (ns) {
-    case 0: return launch_semijoin<ND, 0, SPLIT>(P, smem, grid, st);
-    case 1: return launch_semijoin<ND, (ND >= 1 ? 1 : 0), SPLIT>(P, smem, grid, st);
-    case 2: return launch_semijoin<ND, (ND >= 2 ? 2 : 0), SPLIT>(P, smem, grid, st);
-    case 3: return launch_semijoin<ND, (ND >= 3 ? 3 : 0), SPLIT>(P, smem, grid, st);
-    default: return launch_semijoin<ND, ND, false>(P, smem, grid, st);
-  }
+  semijoin_kernel<ND, NS><<<grid, kSjThreads, smem, st>>>(P);
+  return cudaGetLastError();
 }
 
 template <int ND>
-cudaError_t launch_nd(const SjParams &P, int ns, bool split, size_t smem, int grid, cudaStream_t st) {
-  return split ? launch_nd<ND, true>(P, ns, smem, grid, st) : launch_nd<ND, false>(P, ns, smem, grid, st);
+cudaError_t launch_nd(const SjParams &P, int ns, size_t smem, int grid, cudaStream_t st) {
+  switch (ns) {
+    case 0: return launch_semijoin<ND, 0>(P, smem, grid, st);
+    case 1: return launch_semijoin<ND, (ND >= 1 ? 1 : 0)>(P, smem, grid, st);
+    case 2: return launch_semijoin<ND, (ND >= 2 ? 2 : 0)>(P, smem, grid, st);
+    case 3: return launch_semijoin<ND, (ND >= 3 ? 3 : 0)>(P, smem, grid, st);
+    default: return launch_semijoin<ND, ND>(P, smem, grid, st);
+  }
 }
 
 // Stream-ordered allocation from the library's device pool (esc_scan.cu).
@@ -344,8 +247,7 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
     fk[d] = static_cast<const int32_t *>(fact->data[c]);
     words[d] = (uint32_t)((dim_rows[d] + 31) / 32);
   }
-  // probe order: smallest bitmap first; a prefix of them goes to shared
-  // memory, and the next one, when it fits over a pair of CTAs, is split
+  // probe order: smallest bitmap first; a prefix of them goes to shared memory
   int order[kSjMaxDims] = {0, 1, 2, 3};
   std::stable_sort(order, order + ndims, [&](int a, int b) { return words[a] < words[b]; });
   uint32_t smem_words = 0;
@@ -362,18 +264,6 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
       P.smem_off[i] = smem_words;
       smem_words += (words[d] + 1 + 3) & ~3u;
       ++ns;
-    }
-  }
-  bool split = false;
-  if (ns < ndims) {
-    // words [0, H) in the first CTA of the pair, [H, 2H) in the second; the
-    // zero word (index `words`) falls in the second part
-    const uint32_t H = P.words[ns] / 2 + 1;
-    if ((uint64_t)(smem_words + ((H + 3) & ~3u)) * 4 <= kSjSplitSmemBytes && P.words[ns] >= 1024) {
-      P.smem_off[ns] = smem_words;
-      P.split_half = H;
-      smem_words += (H + 3) & ~3u;
-      split = true;
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -393,10 +283,10 @@ extern "C" esc_status esc_semijoin_counts(const esc_table *fact, const char *con
   const int grid = std::max(1, std::min<int>(sms, (int)((chunks + kSjThreads - 1) / kSjThreads)));
   if (e == cudaSuccess) {
     switch (ndims) {
-      case 1: e = launch_nd<1>(P, ns, split, smem, grid, st); break;
-      case 2: e = launch_nd<2>(P, ns, split, smem, grid, st); break;
-      case 3: e = launch_nd<3>(P, ns, split, smem, grid, st); break;
-      default: e = launch_nd<4>(P, ns, split, smem, grid, st); break;
+      case 1: e = launch_nd<1>(P, ns, smem, grid, st); break;
+      case 2: e = launch_nd<2>(P, ns, smem, grid, st); break;
+      case 3: e = launch_nd<3>(P, ns, smem, grid, st); break;
+      default: e = launch_nd<4>(P, ns, smem, grid, st); break;
     }
   }
   struct {

@@ -120,7 +120,7 @@ def main():
     got = esc.esc_semijoin_counts(fact.handle, ["fk"], [bm[:words]], [70_001])
     want = oracle.semijoin_counts([fk], [mark], [0, 1])
     assert got[1] == want[1] and got[0] == want[0] == len(fk), (got, want)
-    # a dimension too large for one block's shared memory: split over a pair of CTAs
+    # a dimension too large for shared memory (probed in place) beside a small one
     big = 1_000_003
     bw = rng.integers(0, 2**32, (big + 31) // 32, dtype=np.uint64).astype(np.uint32)
     bmark = np.unpackbits(bw.view(np.uint8), bitorder="little")[:big].astype(np.uint8)

@@ -362,9 +362,9 @@ def test_bitmap_and_semijoin(esc):
 @pytest.mark.parametrize("dims_rows", [[0, 37, 1_000_000, 70], [9_000_000, 37, 1_000_000, 70]])
 def test_semijoin_edges(esc, dims_rows):
     """Keys outside [0, rows) (negative, past the end, the int32 extremes), a
-    dimension with no rows, one too large for one CTA's shared memory (split
-    over a pair of CTAs), one too large for that too (probed in place), and
-    bitmaps whose bits past the last row are set."""
+    dimension with no rows, one or two too large for shared memory (probed in
+    place: 1M rows, and 9M rows beside it), and bitmaps whose bits past the
+    last row are set."""
     rng = np.random.default_rng(8)
     n = 200_003
     fk, marks, bms = [], [], []
