@@ -144,9 +144,10 @@ esc_status esc_predicate_compile_many(const esc_table *table, const char *const 
  * fewer amortises per-unit work).  consumer_warps and rows_per_pass pick the
  * scan kernel's block shape: the warps per CTA that evaluate (the CTA has
  * one more, the copy warp) and the rows each lane evaluates per decoded
- * program instruction (8 per 256-row group, one or two groups per pass).
- * The shapes compiled are (15, 16) and (19, 8), which run every program,
- * and (19, 16) and (23, 8), which run programs without a udf.  (0, 0) is
+ * program instruction (8 per 256-row group, one, two or four groups per
+ * pass).  The shapes compiled are (15, 16) and (19, 8), which run every
+ * program, and (19, 16), (23, 8) and (15, 32), which run programs without a
+ * udf.  (0, 0) is
  * automatic: a program reading more than 20 bytes per row runs (19, 8) if
  * it has a udf, else (23, 8); a narrower one (15, 16) or (19, 16).
  * Defaults: 32768, 512, 8, 0, 0.  A batch (esc_batch_prepare,

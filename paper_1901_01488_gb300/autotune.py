@@ -3,7 +3,7 @@
 The knobs are a predicate's esc_tuning: rows staged per tile, staged bytes per
 work unit and work units per SM, and the scan kernel's block shape -- its
 consumer warps per CTA and the rows each lane evaluates per decoded
-instruction (8 per 256-row group, one or two groups per pass).  Results never
+instruction (8 per 256-row group, one, two or four groups per pass).  Results never
 depend on them; speed does, differently for small and large tables, narrow
 and wide predicates, and programs with or without a udf (whose registers
 limit the warps per SM).  Sub-queries are grouped into classes -- (log2 of the
@@ -38,7 +38,7 @@ TILE_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
 # compiled block shapes (consumer warps, rows per lane per pass); the first
 # two run programs with a udf
 SHAPES_UDF: Tuple[Tuple[int, int], ...] = ((15, 16), (19, 8))
-SHAPES: Tuple[Tuple[int, int], ...] = SHAPES_UDF + ((19, 16), (23, 8))
+SHAPES: Tuple[Tuple[int, int], ...] = SHAPES_UDF + ((19, 16), (23, 8), (15, 32))
 WIDTH = {"i32": 4, "i64": 8, "u8": 1, "u16": 2}
 
 

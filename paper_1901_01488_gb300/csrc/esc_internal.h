@@ -36,8 +36,8 @@ struct ScanShape {
   int groups;
   bool udf;
 };
-constexpr ScanShape kScanShapes[] = {{15, 2, true}, {19, 2, false}, {19, 1, true}, {23, 1, false}};
-constexpr int kNumScanShapes = 4;
+constexpr ScanShape kScanShapes[] = {{15, 2, true}, {19, 2, false}, {19, 1, true}, {23, 1, false}, {15, 4, false}};
+constexpr int kNumScanShapes = 5;
 // Automatic choice, from per-predicate timings of the four shapes on a
 // 60M-row table: programs reading more than kWideBytes bytes per row run
 // faster with one group per pass and more warps (their many loads and

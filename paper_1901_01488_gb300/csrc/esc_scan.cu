@@ -414,7 +414,7 @@ __device__ __forceinline__ void eval_groups(const Query *Q, const uint8_t *stage
               for (int k = 0; k < 8; ++k) m[i] |= (uint32_t)(v[i][k] == c) << k;
           }
         }
-      } else if constexpr (UDF) {  // OP_UDF (a program with one never runs on the lean instance)
+      } else if constexpr (UDF) {  // OP_UDF (a program with one runs only on an instance with the udf path)
         const int dt2 = (int)((h.x >> 16) & 0xffu);
         const int w2 = width_of(dt2);
         const uint8_t *col2 = stage + (h.w & 0xffffu);
@@ -1496,7 +1496,7 @@ struct ScanInstance {
     scan_kernel<sh.consumers, sh.udf, sh.groups><<<grid, threads, smem_bytes(), st>>>(L);
   }
 };
-static_assert(kNumScanShapes == 4, "one ScanInstance per shape below");
+static_assert(kNumScanShapes == 5, "one ScanInstance per shape below");
 
 // Launches the scan kernel instance of block shape `shape`.
 void launch_scan_shape(int shape, uint32_t grid, const Launch &L, cudaStream_t st) {
@@ -1504,7 +1504,8 @@ void launch_scan_shape(int shape, uint32_t grid, const Launch &L, cudaStream_t s
     case 0: ScanInstance<0>::launch(grid, L, st); break;
     case 1: ScanInstance<1>::launch(grid, L, st); break;
     case 2: ScanInstance<2>::launch(grid, L, st); break;
-    default: ScanInstance<3>::launch(grid, L, st); break;
+    case 3: ScanInstance<3>::launch(grid, L, st); break;
+    default: ScanInstance<4>::launch(grid, L, st); break;
   }
 }
 
@@ -1512,9 +1513,9 @@ void launch_scan_shape(int shape, uint32_t grid, const Launch &L, cudaStream_t s
 // and the CTAs per SM that every scan instance reaches.
 esc_status configure_kernels(int *blocks_per_sm) {
   const void *fns[kNumScanShapes] = {ScanInstance<0>::fn(), ScanInstance<1>::fn(), ScanInstance<2>::fn(),
-                                     ScanInstance<3>::fn()};
+                                     ScanInstance<3>::fn(), ScanInstance<4>::fn()};
   const int threads[kNumScanShapes] = {ScanInstance<0>::threads, ScanInstance<1>::threads, ScanInstance<2>::threads,
-                                       ScanInstance<3>::threads};
+                                       ScanInstance<3>::threads, ScanInstance<4>::threads};
   int b = 1 << 30;
   for (int i = 0; i < kNumScanShapes; ++i) {
     ESC_CK(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
