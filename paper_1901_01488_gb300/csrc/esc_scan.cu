@@ -14,7 +14,7 @@
 //    with 1-D bulk TMA copies (cp.async.bulk ... mbarrier::complete_tx) into a
 //    ring of kStages stages; the ragged tail of the last tile (< 16 bytes per
 //    column) is copied with plain loads;
-//  * consumers claim runs of one or two 256-row groups of a stage from a
+//  * consumers claim runs of one, two or four 256-row groups of a stage from a
 //    shared counter and interpret the postfix program on 8 rows per lane per
 //    group (one decode per instruction for the run), keeping the
 //    boolean evaluation stack as 8-bit masks in one 64-bit register;
