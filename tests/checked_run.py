@@ -44,8 +44,10 @@ def canaries_intact(capacity, ids, cols):
     return True
 
 
-def check_select(tbl, host, text, proj, capacity=None):
+def check_select(tbl, host, text, proj, capacity=None, tuning=None):
     p = esc.Predicate(tbl, text, proj)
+    if tuning is not None:
+        esc.esc_predicate_set_tuning(p.handle, tuning)
     exp_ids, exp_proj = oracle.select(text, host, proj)
     n = len(exp_ids)
     cap = n if capacity is None else capacity
@@ -87,6 +89,14 @@ def main():
     for pd in datagen.skewed_predicates(200)[::10]:
         check_select(tbl, host, pd.text, datagen.SKEWED_PROJECTION)
         check_select(tbl, host, pd.text, datagen.SKEWED_PROJECTION, capacity=7)
+    # every block shape of the scan kernel, small tiles and units too
+    from paper_1901_01488_gb300.autotune import SHAPES, SHAPES_UDF
+    texts = [pd.text for pd in datagen.skewed_predicates(200)[5::25]]
+    texts.append("udf(price, qty, 97) > 40 AND code7 IN (1, 2, 5)")
+    for j, text in enumerate(texts):
+        for k, shape in enumerate(SHAPES_UDF if "udf" in text else SHAPES):
+            tile = ((2048, 16, 64), (32768, 512, 8), (256, 16, 3))[(j + k) % 3]
+            check_select(tbl, host, text, datagen.SKEWED_PROJECTION, tuning=tile + shape)
     # a batch mixing materialising and count-only sub-queries
     ps = [esc.Predicate(tbl, pd.text, datagen.SKEWED_PROJECTION) for pd in datagen.skewed_predicates(40, seed0=900)]
     exp = [oracle.select(p.text, host, datagen.SKEWED_PROJECTION) for p in ps]
