@@ -14,9 +14,9 @@ selectivities at every size).
     python -m paper_1901_01488_gb300.ncu_profile workload --rows 8000000
     ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum \\
         --clock-control none -k regex:'scan_kernel|write_kernel' --csv \\
-        --log-file gpurun_out/scan_8m.csv \\
+        --log-file scan_8m.csv \\
         python -m paper_1901_01488_gb300.ncu_profile workload --rows 8000000
-    python -m paper_1901_01488_gb300.ncu_profile summarise gpurun_out/scan_8m.csv \\
+    python -m paper_1901_01488_gb300.ncu_profile summarise scan_8m.csv \\
         --rows 8000000 --out profiles/scan_kernel.skewed_8m_200preds.json
 """
 from __future__ import annotations
