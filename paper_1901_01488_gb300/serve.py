@@ -11,7 +11,7 @@ one long wave would hold back every short request in it), compiles their
 predicates and launches them: count requests on one table, when at least
 `shared_min` of them arrived together, share one pass over it
 (esc_selectivity_shared_async); the others run as one batch
-(esc_selectivity_batch_async).
+(esc_selectivity_batch_async), or as a plain call when only one is left.
 Waves on different streams overlap on the GPU.  A request's predicate is
 compiled on a small pool of host threads as soon as it arrives (the library
 call releases the interpreter lock), so the polling thread only admits,
@@ -120,6 +120,7 @@ class Server:
         self.waves = 0
         self.shared_min = shared_min      # count requests per table that share one pass
         self.shared_launches = 0
+        self.single_launches = 0          # waves (or their remainder) of one sub-query, run as a plain call
         self.compile_threads = compile_threads
         self.max_wave_rows = max_wave_rows  # table rows a wave may scan (None: no cap)
         # per wave: launch and completion times (server clock, s), requests,
@@ -207,7 +208,12 @@ class Server:
                 self.shared_launches += 1
                 i = j
             assert i == nshared
-            if i < len(batch):
+            if i == len(batch) - 1:
+                # a lone sub-query: the plain call (less set-up than a batch of one)
+                esc.esc_selectivity_async(self.tables[batch[i].table].handle, preds[i].handle, counts[i:i + 1],
+                                          rows[i], st)
+                self.single_launches += 1
+            elif i < len(batch):
                 rest = rows[i:]
                 esc.esc_selectivity_batch_async([self.tables[r.table].handle for r in batch[i:]],
                                                 [p.handle for p in preds[i:]], counts[i:],
