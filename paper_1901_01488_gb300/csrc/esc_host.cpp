@@ -730,6 +730,14 @@ struct Emitter {
           const uint64_t um = (uint64_t)l.m;
           pool(um < 65536 ? (int64_t)(~0ull / um + 1) : 0);
           pool(um < 65536 ? (int64_t)((1ull << 32) % um) : 0);
+        } else if (ins.op == OP_IN && !l.vals.empty() &&
+                   (uint64_t)l.vals.back() - (uint64_t)l.vals.front() == (uint64_t)(l.vals.size() - 1)) {
+          // the values (sorted, distinct) are one run of consecutive integers:
+          // a single range test, cheaper than a set lookup
+          ins.op = OP_RANGE;
+          ins.lo = l.vals.front();
+          ins.hi = l.vals.back();
+          ins.n = 0;
         } else if (ins.op == OP_IN) {
           ins.n = (uint16_t)l.vals.size();
           bool small = true;

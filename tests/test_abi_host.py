@@ -147,7 +147,10 @@ def test_tests_on_one_operand_merge(esc):
     assert instrs("a BETWEEN 1 AND 5 OR a BETWEEN 6 AND 9 OR a = 20") == [
         "RANGE 0 i32 1 9", "RANGE 0 i32 20 20", "OR"]
     assert instrs("b IN (1, 4, 6) AND b BETWEEN 2 AND 9") == ["IN 0 u8 4,6"]
-    assert instrs("a IN (1, 2, 3) OR a IN (3, 4)") == ["IN 0 i32 1,2,3,4"]
+    assert instrs("a IN (1, 2, 3) OR a IN (3, 4)") == ["RANGE 0 i32 1 4"]          # one run: a range
+    assert instrs("a IN (1, 2, 3) OR a IN (5, 6)") == ["IN 0 i32 1,2,3,5,6"]
+    assert instrs("b IN (8, 5, 7, 6)") == ["RANGE 0 u8 5 8"]
+    assert instrs("b IN (5, 7)") == ["IN 0 u8 5,7"]
     assert instrs("a IN (1, 2, 30) OR a BETWEEN 0 AND 10") == ["RANGE 0 i32 0 10", "RANGE 0 i32 30 30", "OR"]
     # empty conjunction, covering disjunction
     assert instrs("b = 1 AND b IN (4, 6)") == ["FALSE"]
