@@ -65,6 +65,28 @@ def workload(rows: int, preds: int = 200) -> None:
     print("launches: %d count, %d materialising" % (len(ps), len(ps)))
 
 
+def mlp_workload(samples: int) -> None:
+    """The surrogate's kernels for a capture: one forward pass over `samples`
+    rows of 64 bfloat16 features (128 bytes a row), then one gradient pass
+    over the same rows and one Adam step."""
+    import torch
+    sys.path.insert(0, ROOT)
+    from paper_1901_01488_gb300 import build
+    build.build()
+    from paper_1901_01488_gb300 import esc, surrogate
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randn(samples, surrogate.NFEAT, device="cuda", generator=g).to(torch.bfloat16).view(torch.int16)
+    y = torch.randn(samples, device="cuda", generator=g)
+    m = surrogate.Surrogate(esc, seed=3)
+    m.predict(x)
+    grad = torch.zeros_like(m.params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    esc.esc_mlp_grad(x, y, m.wbf, m.params, grad, loss)
+    esc.esc_mlp_adam(m.params, m.wbf, grad, m.m, m.v, 1e-3, 1)
+    torch.cuda.synchronize()
+    print("mlp launches: forward, gradient, adam over %d samples" % samples)
+
+
 def _read_ncu_csv(path: str):
     """Rows of ncu --csv output: (launch id, kernel name, metric, value)."""
     with open(path) as f:
@@ -145,6 +167,8 @@ def main() -> None:
     w = sub.add_parser("workload")
     w.add_argument("--rows", type=int, default=8_000_000)
     w.add_argument("--preds", type=int, default=200)
+    mw = sub.add_parser("mlp")
+    mw.add_argument("--samples", type=int, default=1_000_000)
     s = sub.add_parser("summarise")
     s.add_argument("csv")
     s.add_argument("--rows", type=int, default=8_000_000)
@@ -153,6 +177,8 @@ def main() -> None:
     a = ap.parse_args()
     if a.cmd == "workload":
         workload(a.rows, a.preds)
+    elif a.cmd == "mlp":
+        mlp_workload(a.samples)
     else:
         print(json.dumps(summarise(a.csv, a.rows, a.out, a.command), indent=1))
 
