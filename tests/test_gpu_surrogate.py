@@ -92,7 +92,8 @@ def test_training_gain_over_independence_and_fallback(esc):
     judge), at a median no more than 10 % higher.  With exact ESC as the fallback (the surrogate trusted only in
     the selectivity decades where a calibration split kept its q-error
     within 2 for 95% of predicates), most held-out predicates still need no
-    exact sub-query, and the answers stay within the bound."""
+    exact sub-query, and the answers stay within the bound.  A seeded subset
+    of the labels is recounted by the oracle."""
     from paper_1901_01488_gb300 import surrogate as S
     t = datagen.skewed_table(2_000_000, seed=40, device="cuda")
     table = esc.Table.from_datagen(t)
@@ -103,6 +104,10 @@ def test_training_gain_over_independence_and_fallback(esc):
     targets = 10.0 ** rng.uniform(-6, np.log10(0.9), n)
     texts = [datagen.random_predicate(900_000 + j, float(targets[j])).text for j in range(n)]
     counts = S.exact_counts(esc, table, texts)
+    # the labels are exact: a seeded subset recounted by the oracle
+    import oracle
+    for j in np.random.default_rng(11).choice(n, 48, replace=False):
+        assert counts[j] == oracle.count(texts[j], host), texts[j]
     L = S.listings(esc, table, texts)
     X = syn.features_batch(L)
     base = syn.base_log(L, t.nrows)                                  # independence, log10
