@@ -869,7 +869,7 @@ esc_status esc_table_create(const esc_column *cols, int32_t ncols, uint64_t nrow
   if (!out) return fail(ESC_EINVAL, "esc_table_create: out is NULL");
   *out = nullptr;
   if (!cols || ncols < 1 || ncols > 64) return fail(ESC_EINVAL, "esc_table_create: need 1..64 columns");
-  if (nrows >= (1ull << 32)) return fail(ESC_EINVAL, "esc_table_create: nrows must be < 2^32");
+  if (nrows > ESC_MAX_ROWS) return fail(ESC_EINVAL, "esc_table_create: nrows must be at most 2^32 - 2^16");
   std::unique_ptr<esc_table> t(new (std::nothrow) esc_table);
   if (!t) return fail(ESC_ENOMEM, "esc_table_create: out of host memory");
   t->nrows = nrows;

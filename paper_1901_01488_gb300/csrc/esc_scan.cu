@@ -1692,6 +1692,8 @@ void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
     if (I.op == OP_RANGE || I.op == OP_IN || I.op == OP_INSET || I.op == OP_UDF) I.soff = (uint16_t)q.stage_off[I.ref];
     if (I.op == OP_UDF) I.soff2 = (uint16_t)q.stage_off[I.ref2];
   }
+  // nrows <= ESC_MAX_ROWS (2^32 - 2^16): the rounded-up extents here and in
+  // the kernels (tiles, groups, 32-bit words, compaction units) stay below 2^32
   q.ntiles = (q.nrows + q.tile_rows - 1) / q.tile_rows;
   q.gmax = q.tile_rows / kGroup;
   const uint64_t tile_bytes = (uint64_t)q.tile_rows * std::max<uint32_t>(bpr, 1);

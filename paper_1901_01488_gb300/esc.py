@@ -29,6 +29,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 ESC_OK, ESC_EINVAL, ESC_ETYPE, ESC_ENOMEM, ESC_ETRUNC, ESC_ETIMEOUT, ESC_EBUSY, ESC_ECUDA, ESC_EBOUNDS = range(9)
 DTYPE_CODE = {"i32": 0, "i64": 1, "u8": 2, "u16": 3}
 WIDTH = {"i32": 4, "i64": 8, "u8": 1, "u16": 2}
+MAX_ROWS = (1 << 32) - (1 << 16)   # ESC_MAX_ROWS: rows a table may hold
 TORCH_DTYPE = {"i32": torch.int32, "i64": torch.int64, "u8": torch.uint8, "u16": torch.int16}
 
 
@@ -133,6 +134,10 @@ def esc_table_create(columns: Sequence[Tuple[str, str, torch.Tensor]], nrows: in
 
 def esc_table_destroy(handle: int) -> None:
     _lib.esc_table_destroy(handle)
+
+
+def esc_table_nrows(handle: int) -> int:
+    return int(_lib.esc_table_nrows(handle))
 
 
 def esc_predicate_compile(table: int, text: str, proj: Sequence[str] = ()) -> int:

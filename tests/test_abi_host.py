@@ -211,8 +211,13 @@ def test_table_create_errors(esc):
         esc.esc_table_create([("1a", "i32", x)], 64)
     with pytest.raises(esc.EscError):
         esc.esc_table_create([("a", "i32", x)], 1 << 32)
-    h = esc.esc_table_create([("a", "i32", x)], 0)
-    esc.esc_table_destroy(h)
+    with pytest.raises(esc.EscError) as ei:
+        esc.esc_table_create([("a", "i32", x)], esc.MAX_ROWS + 1)    # an extent would pass 2^32
+    assert ei.value.status == esc.ESC_EINVAL
+    for n in (0, esc.MAX_ROWS):            # creating a table only records the pointers
+        h = esc.esc_table_create([("a", "i32", x)], n)
+        assert esc.esc_table_nrows(h) == n
+        esc.esc_table_destroy(h)
 
 
 def test_udf_magic_divides_exactly(esc):
