@@ -114,3 +114,38 @@ def test_shared_batch_and_noalloc_at_the_row_limit(esc, big):
     with pytest.raises(esc.EscError) as ei:
         esc.esc_selectivity_noalloc(t.handle, sel.handle, sel.alloc_rows(n_eq(n, 7)))
     assert ei.value.status == esc.ESC_EINVAL
+
+
+def test_semijoin_at_the_row_limit(esc):
+    """Semi-join counts over a fact table of 2^32 - 2^16 rows: fk0 = row mod
+    1000 and fk1 = row mod 1024 into two dimensions of 1000 rows (keys
+    1000..1023 of fk1 match nothing).  The keys repeat every 128,000 rows, so
+    the expected counts are the oracle's nested loop over one period times
+    the number of whole periods, plus the oracle over the remaining rows."""
+    n = esc.MAX_ROWS
+    period = 128_000
+    fk = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(2)]
+    step = 1 << 28
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        r = torch.arange(s, e, dtype=torch.int64, device="cuda")
+        fk[0][s:e] = (r % 1000).to(torch.int32)
+        fk[1][s:e] = (r % 1024).to(torch.int32)
+        del r
+    fact = esc.Table([("fk0", "i32", fk[0]), ("fk1", "i32", fk[1])], n)
+    keys = np.arange(1000)
+    marks = [(keys % 3 == 0).astype(np.uint8), (keys % 5 != 2).astype(np.uint8)]
+    bms = [torch.from_numpy(np.packbits(m, bitorder="little").view(np.uint8).copy()) for m in marks]
+    bms = [torch.nn.functional.pad(b, (0, (-b.numel()) % 4)).view(torch.int32).cuda() for b in bms]
+    got = esc.esc_semijoin_counts(fact.handle, ["fk0", "fk1"], bms, [1000, 1000])
+    r = np.arange(period, dtype=np.int64)
+    one = [(r % 1000).astype(np.int32), (r % 1024).astype(np.int32)]
+    q, rem = divmod(n, period)
+    per = oracle.semijoin_counts(one, marks, [0, 1, 2, 3])
+    part = oracle.semijoin_counts([c[:rem] for c in one], marks, [0, 1, 2, 3])
+    want = [q * per[s] + part[s] for s in range(4)]
+    assert want[0] == n
+    assert list(got) == want, (got, want)
+    fact.close()
+    del fk
+    torch.cuda.empty_cache()
