@@ -25,7 +25,7 @@ constexpr int kMaxDepth = 8;    // evaluation stack: 8 masks of 8 bits in one u6
 constexpr int kV = 8;           // rows per lane per group
 constexpr int kGroup = 256;     // rows per warp group (32 lanes x 8 rows)
 constexpr int kMaxTileRows = 32768;
-constexpr int kMaxUnitRows = 65536;   // rows per scan work unit at most, and per compaction unit
+constexpr int kMaxUnitRows = 65536;   // rows per scan work unit at most, and per compaction unit at most
 
 // Block shapes of the scan kernel, one compiled instance each: consumer
 // warps per CTA, 256-row groups each warp evaluates per decoded instruction
@@ -121,9 +121,10 @@ struct Query {
   int8_t proj_ref[kMaxProj];      // stage slot of the projected column (informational), or -1
   uint32_t is_const;      // the program reads no column: no work units, answered by the constant kernel
   uint32_t const_value;   // its value (0 or 1) when is_const
-  uint32_t nwunits;       // compaction units: kMaxUnitRows rows each (write-kernel blocks, unit totals)
+  uint32_t nwunits;       // compaction units (write-kernel blocks, unit totals), wunit_groups groups each
   uint32_t unit_big;      // work units 0..unit_big-1 hold unit_tiles tiles, the later ones one tile
-  uint32_t pad2[4];
+  uint32_t wunit_groups;  // groups per compaction unit (1..kMaxUnitRows / kGroup)
+  uint32_t pad2[3];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

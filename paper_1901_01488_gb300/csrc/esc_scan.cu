@@ -779,9 +779,9 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           if (mode == MODE_COUNT) continue;
           uint32_t word = 0;
           if (mode == MODE_SELECT) {
-            // the group's compaction unit (kMaxUnitGroups groups): flush the
+            // the group's compaction unit (wunit_groups groups): flush the
             // running total when it changes (warp-uniform)
-            const uint32_t wu = (mt.tile * Q->gmax + (uint32_t)gs[i]) / (uint32_t)kMaxUnitGroups;
+            const uint32_t wu = (mt.tile * Q->gmax + (uint32_t)gs[i]) / Q->wunit_groups;
             if (!ESC_INB(hdr, wu < Q->nwunits, 16, wu)) continue;
             unsigned long long *up = Q->unit_total + wu;
             if (up != uacc_ptr) {
@@ -836,10 +836,11 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
 }
 
 // ------------------------------------------------------------------ the write kernel
-// Second pass of ordered compaction, one block per compaction unit
-// (kMaxUnitRows = 65536 rows, 256 groups of 256 rows: one thread per group;
-// independent of the scan's work units, so that a sparse selection runs as
-// few, full blocks whatever the predicate's read width).
+// Second pass of ordered compaction, one block per compaction unit (at most
+// kMaxUnitGroups = 256 groups of 256 rows: one thread per group; sized per
+// query so that the blocks fill whole waves of the GPU, see
+// layout_write_units; independent of the scan's work units, whatever the
+// predicate's read width).
 //  1. The unit's first output slot: a decoupled look-back over the units
 //     before it (Merrill & Garland 2016).  Every unit's aggregate is already
 //     final (written by the scan kernel), so the look-back adds aggregates
@@ -860,6 +861,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
 
 constexpr int kWriteThreads = 256;
 constexpr int kWriteWarps = kWriteThreads / 32;
+constexpr int kWriteBlocksPerSm = 4;     // resident write-kernel blocks per SM (registers and shared memory)
 static_assert(kMaxUnitGroups <= kWriteThreads, "one write-kernel thread per group of a unit");
 constexpr uint32_t kDenseMin = 64;       // qualifying rows of a group for the dense path
 constexpr uint32_t kRawBytes = 2048;     // per warp: a dense group's projected values (<= 8 B per row at once)
@@ -1047,7 +1049,7 @@ __device__ __forceinline__ void lookback_load(const unsigned long long *st, cons
   }
 }
 
-__global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(kWriteThreads, kWriteBlocksPerSm) write_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(16) uint8_t wsmem[];
   __shared__ GatherInfo G;
   __shared__ uint32_t wsum[kWriteWarps];
@@ -1078,7 +1080,7 @@ __global__ void __launch_bounds__(kWriteThreads, 4) write_kernel(const __grid_co
   }
   const uint32_t u = blockIdx.x - Q->wunit_base;
   if (!ESC_INB(L.hdr, u < Q->nwunits, 20, u)) return;  // uniform: the whole block
-  const uint32_t urows = kMaxUnitRows;
+  const uint32_t urows = Q->wunit_groups * kGroup;
   const uint32_t urow0 = u * urows;
   const uint32_t rows = min(urows, Q->nrows - urow0);
   const int ng = (int)((rows + kGroup - 1) / kGroup);
@@ -1675,10 +1677,27 @@ uint32_t tile_rows_for(const Query &q, const esc_tuning &tu) {
   return std::min<uint32_t>(std::min<uint32_t>(t, kMaxTileRows), tu.max_tile_rows);
 }
 
+// Compaction units: one write-kernel block each.  slots == 0: units of
+// kMaxUnitGroups groups.  Otherwise the fewest whole waves of `slots` blocks
+// that full-size units need, with units just large enough to fill them: the
+// write kernel's blocks take about equal time, so a last wave only partly
+// full would leave that share of the GPU idle for a whole block's time.
+void layout_write_units(Query &q, int slots) {
+  const uint64_t ngroups = ((uint64_t)q.nrows + kGroup - 1) / kGroup;
+  uint64_t ug = kMaxUnitGroups;
+  if (slots > 0) {
+    const uint64_t wave = (uint64_t)slots * kMaxUnitGroups;
+    const uint64_t waves = std::max<uint64_t>(1, (ngroups + wave - 1) / wave);
+    ug = std::min<uint64_t>(kMaxUnitGroups, std::max<uint64_t>(1, (ngroups + waves * slots - 1) / (waves * slots)));
+  }
+  q.wunit_groups = (uint32_t)ug;
+  q.nwunits = (uint32_t)((ngroups + ug - 1) / ug);
+}
+
 // Stage layout (read columns back to back, each slice 128-byte aligned), the
 // work units (consecutive tiles claimed with one ticket: at most ~512 KB of
 // staged columns, >= 8 per SM when the table is large enough), and the
-// compaction units (kMaxUnitRows rows each, one write-kernel block).
+// compaction units (layout_write_units).
 void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
   q.tile_rows = tile_rows_for(q, tu);
   uint32_t off = 0, bpr = 0;
@@ -1705,7 +1724,7 @@ void layout_stage(Query &q, int sms, const esc_tuning &tu = kDefaultTuning) {
   const uint32_t tail = std::min<uint32_t>(q.ntiles, (uint32_t)(kTailTilesPerSm * sms));
   q.unit_big = (q.ntiles - tail) / q.unit_tiles;
   q.nunits = q.unit_big + (q.ntiles - q.unit_big * q.unit_tiles);
-  q.nwunits = (uint32_t)(((uint64_t)q.nrows + kMaxUnitRows - 1) / kMaxUnitRows);
+  layout_write_units(q, sms * kWriteBlocksPerSm);
 }
 
 
@@ -1971,6 +1990,7 @@ esc_status batch_prepare(const esc_table *const *tables, const esc_pred *const *
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
                            &qin[i])) != ESC_OK)
       return s;
+    layout_write_units(qin[i], 0);  // one write grid for all queries: full-size units
     mark_constant(qin[i]);
   }
   // smallest work first (stable: equal work keeps the caller's order)
@@ -2204,6 +2224,7 @@ esc_status esc_selectivity_batch_async(const esc_table *const *tables, const esc
     if ((s = prepare_query(tables[i], preds[i], compact ? r : nullptr, compact ? MODE_SELECT : MODE_COUNT,
                            &qs[i])) != ESC_OK)
       return s;
+    layout_write_units(qs[i], 0);  // one write grid for all queries: full-size units
     mark_constant(qs[i]);
     if (qs[i].is_const) cidx.push_back((uint32_t)i);
     qs[i].unit_base = (uint32_t)units;

@@ -53,12 +53,15 @@ def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
     """Device memory a request holds while in flight: its compiled query and
     counters in the launch (4 KB), and when it materialises, the library's
     scratch (the selection bitmap, 1/8 byte per row rounded up to whole tiles
-    of at most 32768 rows, 16 bytes per compaction unit of 65536 rows,
-    headers) and its output buffers."""
+    of at most 32768 rows; 16 bytes per compaction unit, of which there are
+    at most one per 256-row group and at most one per 65536 rows plus one
+    wave of write-kernel blocks, taken as 1024; headers) and its output
+    buffers."""
     base = 4096
     if not req.proj:
         return base
-    scratch = nrows // 8 + 16 * ((nrows + 65535) // 65536) + 8192
+    units = min((nrows + 255) // 256, (nrows + 65535) // 65536 + 1024)
+    scratch = nrows // 8 + 16 * units + 8192
     return base + scratch + req.capacity * (4 + sum(widths[c] for c in req.proj))
 
 

@@ -86,11 +86,15 @@ def test_request_bytes():
     count_only = Request(0, 0, "TRUE", 0.0)
     assert request_bytes(60_000_000, count_only, w) == 4096      # a compiled query is ~3.7 KB
     r = Request(0, 0, "TRUE", 0.0, proj=("a", "b"), capacity=1000)
-    for n in (1, 255, 256, 65536, 65537, 60_000_000, 600_000_000):
-        # the bitmap rounded to a whole tile (<= 32768 rows), the unit words, the outputs
-        need = (n + 32767) // 8 + 16 * ((n + 65535) // 65536) + 1000 * (4 + 12)
+    for n in (1, 255, 256, 65536, 65537, 1_000_000, 8_000_000, 60_000_000, 600_000_000):
+        # the bitmap rounded to a whole tile (<= 32768 rows), the unit words
+        # (compaction units filling whole waves of 152 SMs x 4 blocks), the outputs
+        groups, slots = (n + 255) // 256, 152 * 4
+        waves = max(1, -(-groups // (256 * slots)))
+        ug = min(256, max(1, -(-groups // (waves * slots))))
+        need = (n + 32767) // 8 + 16 * -(-groups // ug) + 1000 * (4 + 12)
         assert request_bytes(n, r, w) >= need
-        assert request_bytes(n, r, w) - need <= 16384
+        assert request_bytes(n, r, w) - need <= 16384 + 16 * 1024
 
 
 def test_poisson_arrivals_and_latency_summary():
