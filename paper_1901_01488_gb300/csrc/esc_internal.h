@@ -124,7 +124,8 @@ struct Query {
   uint32_t nwunits;       // compaction units (write-kernel blocks, unit totals), wunit_groups groups each
   uint32_t unit_big;      // work units 0..unit_big-1 hold unit_tiles tiles, the later ones one tile
   uint32_t wunit_groups;  // groups per compaction unit (1..kMaxUnitRows / kGroup)
-  uint32_t pad2[3];
+  uint32_t wunit_recip;   // ceil(2^32 / wunit_groups), 0 for one group: group -> unit by a multiply-high
+  uint32_t pad2[2];
   const uint8_t *ref_ptr[kMaxRef];
   const uint8_t *proj_ptr[kMaxProj];
   void *out_proj[kMaxProj];

@@ -781,7 +781,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1) scan_kernel(const __grid_con
           if (mode == MODE_SELECT) {
             // the group's compaction unit (wunit_groups groups): flush the
             // running total when it changes (warp-uniform)
-            const uint32_t wu = (mt.tile * Q->gmax + (uint32_t)gs[i]) / Q->wunit_groups;
+            const uint32_t gix = mt.tile * Q->gmax + (uint32_t)gs[i];
+            const uint32_t wu = Q->wunit_recip ? __umulhi(gix, Q->wunit_recip) : gix;
             if (!ESC_INB(hdr, wu < Q->nwunits, 16, wu)) continue;
             unsigned long long *up = Q->unit_total + wu;
             if (up != uacc_ptr) {
@@ -1691,6 +1692,10 @@ void layout_write_units(Query &q, int slots) {
     ug = std::min<uint64_t>(kMaxUnitGroups, std::max<uint64_t>(1, (ngroups + waves * slots - 1) / (waves * slots)));
   }
   q.wunit_groups = (uint32_t)ug;
+  // group g's unit is g / ug = umulhi(g, ceil(2^32 / ug)): with ug * M = 2^32 + e,
+  // e < ug, the quotient is exact while g * e < 2^32, and every group index
+  // (< ESC_MAX_ROWS / 256 < 2^24) keeps g * 255 below 2^32
+  q.wunit_recip = ug > 1 ? (uint32_t)(((1ull << 32) + ug - 1) / ug) : 0u;
   q.nwunits = (uint32_t)((ngroups + ug - 1) / ug);
 }
 
