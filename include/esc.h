@@ -85,9 +85,9 @@ typedef struct esc_rows {
 /* Columnar table store (Sec. 2: column-wise in-memory tables).  Registers
  * `ncols` (1..64) borrowed device columns of `nrows` rows each (0 to
  * ESC_MAX_ROWS = 2^32 - 2^16: row ids are uint32, and every extent rounded up
- * to a compaction unit, at most 65536 rows, stays below 2^32).  Column names must be distinct identifiers.  Each `data`
- * must be 16-byte aligned (ESC_EINVAL otherwise) and stay valid until
- * esc_table_destroy.  Unknown dtypes give ESC_ETYPE.  *out is owned by the
+ * to a compaction unit, at most 65536 rows, stays below 2^32).  Column
+ * names must be distinct identifiers.  Each `data` must be 16-byte aligned
+ * (ESC_EINVAL otherwise) and stay valid until esc_table_destroy.  Unknown dtypes give ESC_ETYPE.  *out is owned by the
  * caller and released with esc_table_destroy. */
 esc_status esc_table_create(const esc_column *cols, int32_t ncols, uint64_t nrows,
                             esc_table **out);
