@@ -117,6 +117,11 @@ class Server:
         self.max_batch = max_batch
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        # per stream: the wave's counts on the device (every library call
+        # overwrites its range, so no fill is needed) and a pinned copy the
+        # host reads once the wave's event has completed (no blocking read)
+        self.dev_counts = [torch.empty(max_batch, dtype=torch.int64, device=self.device) for _ in range(streams)]
+        self.host_counts = [torch.empty(max_batch, dtype=torch.int64, pin_memory=True) for _ in range(streams)]
         self.widths = [{n: esc.WIDTH[d] for n, d, _ in t.columns} for t in tables]
         self.in_flight_bytes = 0
         self.peak_bytes = 0
@@ -158,7 +163,7 @@ class Server:
                 if w is not None and w["event"].query():
                     t_done = clock() - t0
                     w["log"]["done"] = t_done
-                    counts = w["counts"].tolist()
+                    counts = w["host"].tolist()
                     for r, c in zip(w["reqs"], counts):
                         r.count = int(c)
                         r.done = t_done
@@ -191,8 +196,8 @@ class Server:
         preds = []
         rows = []
         with torch.cuda.stream(st):
-            # outputs and counts are allocated (and zeroed) on the wave's own
-            # stream, so that the kernels below are ordered after the fill
+            # outputs are allocated on the wave's own stream, so that the
+            # kernels below are ordered after their allocation
             for r in batch:
                 p = r.pred.result()
                 r.pred = p
@@ -202,7 +207,7 @@ class Server:
                     rows.append(r.rows)
                 else:
                     rows.append(None)
-            counts = torch.zeros(len(batch), dtype=torch.int64, device=self.device)
+            counts = self.dev_counts[k][:len(batch)]
             i = 0
             for g in groups:
                 j = i + len(g)
@@ -221,6 +226,8 @@ class Server:
                 esc.esc_selectivity_batch_async([self.tables[r.table].handle for r in batch[i:]],
                                                 [p.handle for p in preds[i:]], counts[i:],
                                                 rest if any(x is not None for x in rest) else None, None, st)
+            host = self.host_counts[k][:len(batch)]
+            host.copy_(counts, non_blocking=True)   # ordered before the event on the wave's stream
             ev = torch.cuda.Event()
             ev.record(st)
         self.in_flight_bytes += nbytes
@@ -228,7 +235,7 @@ class Server:
         self.waves += 1
         log = {"requests": len(batch), "shared": len(groups),
                "rows": sum(self.tables[r.table].nrows for r in batch)}
-        slots[k] = {"reqs": batch, "counts": counts, "event": ev, "bytes": nbytes, "preds": preds, "log": log}
+        slots[k] = {"reqs": batch, "host": host, "event": ev, "bytes": nbytes, "preds": preds, "log": log}
 
 
 @contextlib.contextmanager
@@ -282,6 +289,14 @@ class PlainServer:
         pool = ThreadPoolExecutor(self.compile_threads)
         inflight: Deque[tuple] = deque()
         compiling: Deque[Request] = deque()
+        # count slots: each request's count on the device (the library call
+        # stores it, no fill needed) and a pinned copy read once its event
+        # has completed; a slot goes back to the free list then
+        nslots = 1 << 15
+        dev_counts = torch.empty(nslots, dtype=torch.int64, device=self.device)
+        host_counts = torch.empty(nslots, dtype=torch.int64, pin_memory=True)
+        host_view = host_counts.numpy()
+        free = deque(range(nslots))
         t0 = clock()
         done_n, k = 0, 0
         while done_n < len(requests):
@@ -291,25 +306,28 @@ class PlainServer:
                 r = queue.popleft()
                 r.pred = pool.submit(lambda r=r: esc.Predicate(self.tables[r.table], r.text, tuple(r.proj)))
                 compiling.append(r)
-            while compiling and compiling[0].pred.done():
+            while compiling and compiling[0].pred.done() and free:
                 r = compiling.popleft()
                 r.pred = r.pred.result()
                 st = self.streams[k % len(self.streams)]
                 k += 1
+                s = free.popleft()
+                cnt = dev_counts[s:s + 1]
                 with torch.cuda.stream(st):
-                    cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
                     if r.proj:
                         r.rows = r.pred.alloc_rows(max(1, r.capacity), device=self.device)
                     esc.esc_selectivity_async(self.tables[r.table].handle, r.pred.handle, cnt, r.rows, st)
+                    host_counts[s:s + 1].copy_(cnt, non_blocking=True)
                     ev = torch.cuda.Event()
                     ev.record(st)
-                inflight.append((r, cnt, ev))
+                inflight.append((r, s, ev))
                 progressed = True
             keep: Deque[tuple] = deque()
             for item in inflight:
-                r, cnt, ev = item
+                r, s, ev = item
                 if ev.query():
-                    r.count = int(cnt.item())
+                    r.count = int(host_view[s])
+                    free.append(s)
                     r.done = clock() - t0
                     done_n += 1
                     progressed = True
