@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=20_000, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20_000.0, help="serve: highest arrival rate of the sweep (per s)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: seconds of arrivals per rate")
+    ap.add_argument("--compile-threads", type=int, default=0,
+                    help="serve: host threads compiling predicates (0: on the polling thread)")
     ap.add_argument("--max-wave-rows", type=int, default=1_200_000_000,
                     help="serve: table rows one wave may scan (0: no cap)")
     ap.add_argument("--rates", type=str, default="", help="serve: comma-separated arrival rates (default: a sweep)")
@@ -594,10 +596,11 @@ def run_serve(args):
     levels = {}
     for rate in rates:
         n = int(min(nmax, max(2_000, rate * args.serve_seconds)))
-        srv = serve.Server(esc, etabs, mem_budget=16 << 30, max_batch=512, streams=4, max_wave_rows=cap)
+        srv = serve.Server(esc, etabs, mem_budget=16 << 30, max_batch=512, streams=4, max_wave_rows=cap,
+                           compile_threads=args.compile_threads)
         srv.run(requests(rate, min(512, n)))                                   # warm-up
         batched = srv.run(requests(rate, n))
-        plain = serve.PlainServer(esc, etabs, streams=4)
+        plain = serve.PlainServer(esc, etabs, streams=4, compile_threads=args.compile_threads)
         plain.run(requests(rate, min(512, n)))
         single = plain.run(requests(rate, n))
         for a, b in zip(batched, single):

@@ -4,19 +4,19 @@ Not in the paper (there, the optimizer issues one sub-query per table with
 a selection, Sec. 2); this is the serving pattern around it.  Requests
 (table, predicate) arrive over time.  A host loop keeps `streams` waves in
 flight: whenever a stream is free it admits every request that has arrived,
-up to `max_batch`, within the device-memory budget (each request reserves
-the scratch and output bytes its materialisation needs) and within
-`max_wave_rows` table rows scanned (a wave's requests complete together, so
-one long wave would hold back every short request in it), compiles their
-predicates and launches them: count requests on one table, when at least
-`shared_min` of them arrived together, share one pass over it
+up to `max_batch`, within the device-memory budget (each request reserves the scratch and output bytes
+its materialisation needs) and within `max_wave_rows` table rows scanned (a
+wave's requests complete together, so one long wave would hold back every
+short request in it), and launches them: count requests on one table, when
+at least `shared_min` of them arrived together, share one pass over it
 (esc_selectivity_shared_async); the others run as one batch
 (esc_selectivity_batch_async), or as a plain call when only one is left.
 Waves on different streams overlap on the GPU.  A request's predicate is
-compiled on a small pool of host threads as soon as it arrives (the library
-call releases the interpreter lock), so the polling thread only admits,
-launches and observes completions.  A request's latency runs from its
-arrival to the host observing its wave's completion event.
+compiled when it arrives, on the polling thread by default (about 8 us);
+`compile_threads` > 0 hands compilation to a pool of host threads instead,
+which measured slower: each request then waits for a thread hand-off.  A
+request's latency runs from its arrival to the host observing its wave's
+completion event.
 
 `PlainServer` is the baseline without batching: every request is its own
 sub-query call, launched when it arrives (round robin over the streams).
@@ -47,6 +47,25 @@ class Request:
     done: Optional[float] = None
     rows: Optional[tuple] = None
     pred: Optional[object] = None       # compiled predicate (a future while compiling)
+
+
+class _Ready:
+    """A predicate compiled on the polling thread, in the shape of a finished
+    future (compile_threads = 0)."""
+    __slots__ = ("value",)
+
+    def __init__(self, value):
+        self.value = value
+
+    def result(self):
+        return self.value
+
+    def done(self) -> bool:
+        return True
+
+
+def _compile_pool(threads: int) -> Optional[ThreadPoolExecutor]:
+    return ThreadPoolExecutor(threads) if threads > 0 else None
 
 
 def request_bytes(nrows: int, req: Request, widths: Dict[str, int]) -> int:
@@ -109,7 +128,7 @@ def wave_groups(batch: Sequence[Request], shared_min: int) -> Tuple[List[List[Re
 
 class Server:
     def __init__(self, esc, tables, mem_budget: int = 8 << 30, max_batch: int = 512, streams: int = 2,
-                 device="cuda", shared_min: int = 8, compile_threads: int = 4,
+                 device="cuda", shared_min: int = 8, compile_threads: int = 0,
                  max_wave_rows: Optional[int] = 1_200_000_000):
         self.esc = esc
         self.tables = tables
@@ -148,14 +167,14 @@ class Server:
         pending: Deque[Request] = deque()
         queue = deque(sorted(requests, key=lambda r: r.arrival))
         slots: List[Optional[dict]] = [None] * len(self.streams)
-        pool = ThreadPoolExecutor(self.compile_threads)
+        pool = _compile_pool(self.compile_threads)
         t0 = clock()
         done_n = 0
         while done_n < len(requests):
             now = clock() - t0
             while queue and queue[0].arrival <= now:
                 r = queue.popleft()
-                r.pred = pool.submit(self._compile, r)   # compiled off the polling thread
+                r.pred = pool.submit(self._compile, r) if pool else _Ready(self._compile(r))
                 pending.append(r)
             progressed = False
             for k, st in enumerate(self.streams):
@@ -184,7 +203,8 @@ class Server:
                         progressed = True
             if not progressed:
                 time.sleep(0)
-        pool.shutdown(wait=True)
+        if pool:
+            pool.shutdown(wait=True)
         return list(requests)
 
     def _launch(self, batch: List[Request], k: int, st, nbytes: int, slots) -> None:
@@ -272,7 +292,7 @@ class PlainServer:
     over `streams`); the baseline that continuous batching is measured
     against.  Completion is observed by polling each request's event."""
 
-    def __init__(self, esc, tables, streams: int = 2, device="cuda", compile_threads: int = 4):
+    def __init__(self, esc, tables, streams: int = 2, device="cuda", compile_threads: int = 0):
         self.esc = esc
         self.tables = tables
         self.device = torch.device(device)
@@ -286,7 +306,7 @@ class PlainServer:
     def _run(self, requests: Sequence[Request], clock) -> List[Request]:
         esc = self.esc
         queue = deque(sorted(requests, key=lambda r: r.arrival))
-        pool = ThreadPoolExecutor(self.compile_threads)
+        pool = _compile_pool(self.compile_threads)
         inflight: Deque[tuple] = deque()
         compiling: Deque[Request] = deque()
         # count slots: each request's count on the device (the library call
@@ -304,7 +324,10 @@ class PlainServer:
             progressed = False
             while queue and queue[0].arrival <= now:
                 r = queue.popleft()
-                r.pred = pool.submit(lambda r=r: esc.Predicate(self.tables[r.table], r.text, tuple(r.proj)))
+                if pool:
+                    r.pred = pool.submit(lambda r=r: esc.Predicate(self.tables[r.table], r.text, tuple(r.proj)))
+                else:
+                    r.pred = _Ready(esc.Predicate(self.tables[r.table], r.text, tuple(r.proj)))
                 compiling.append(r)
             while compiling and compiling[0].pred.done() and free:
                 r = compiling.popleft()
@@ -336,5 +359,6 @@ class PlainServer:
             inflight = keep
             if not progressed:
                 time.sleep(0)
-        pool.shutdown(wait=True)
+        if pool:
+            pool.shutdown(wait=True)
         return list(requests)
