@@ -615,7 +615,8 @@ def run_serve(args):
            "config": {"workload": "Poisson arrivals over tables " + str(list(sizes)) + "; every fourth request "
                                   "materialises (key, day, price) when it selects <= 1M rows; continuous batching "
                                   "on 4 streams, admission by device memory and by rows scanned per wave; "
-                                  "predicates compiled on 4 host threads",
+                                  + ("predicates compiled on %d host threads" % args.compile_threads
+                                     if args.compile_threads > 0 else "predicates compiled on the polling thread"),
                       "max_wave_rows": cap,
                       "rates_per_s": rates},
            "levels": levels,
