@@ -365,9 +365,16 @@ esc_status esc_selftest_wait_timeout(uint64_t limit_ns, void *stream);
  * esc_build_checked(&flag): *flag = 1 in the checked build
  * (libesc_checked.so), whose kernels test the indices they are about to use
  * and report ESC_EBOUNDS (with the site and the index in the message)
- * instead of touching memory out of range; 0 in the release build. */
+ * instead of touching memory out of range; 0 in the release build.
+ * esc_debug_write_units(nrows, slots, ...): the compaction units a
+ * materialising call on a table of nrows rows (<= ESC_MAX_ROWS) uses when
+ * the GPU holds `slots` write-kernel blocks at once (slots = 0: the
+ * full-size units of a batch); out (host, 3 entries): the groups of 256
+ * rows per unit, the number of units, and the reciprocal that maps a group
+ * to its unit (ceil(2^32 / groups per unit), 0 for one group). */
 esc_status esc_debug_fail_allocs(int32_t n);
 esc_status esc_build_checked(int32_t *flag);
+esc_status esc_debug_write_units(uint64_t nrows, int32_t slots, uint32_t *out);
 
 #ifdef __cplusplus
 }

@@ -818,6 +818,9 @@ esc_status device_status(const ScratchHdr &h, const char *where) {
   return fail((esc_status)h.status, std::string(where) + ": a bounded device-side wait gave up");
 }
 
+// Compaction-unit layout of a materialising call (defined with the kernels).
+void layout_write_units(Query &q, int slots);
+
 }  // namespace esc
 
 using namespace esc;
@@ -845,6 +848,19 @@ const char *esc_status_string(esc_status s) {
 esc_status esc_debug_fail_allocs(int32_t n) {
   if (n < 0) return fail(ESC_EINVAL, "esc_debug_fail_allocs: n must be >= 0");
   g_fail_allocs.store(n);
+  clear_error();
+  return ESC_OK;
+}
+
+esc_status esc_debug_write_units(uint64_t nrows, int32_t slots, uint32_t *out) {
+  if (!out || nrows > ESC_MAX_ROWS || slots < 0) return fail(ESC_EINVAL, "esc_debug_write_units: bad argument");
+  esc::Query q;
+  std::memset(&q, 0, sizeof q);
+  q.nrows = (uint32_t)nrows;
+  esc::layout_write_units(q, slots);
+  out[0] = q.wunit_groups;
+  out[1] = q.nwunits;
+  out[2] = q.wunit_recip;
   clear_error();
   return ESC_OK;
 }

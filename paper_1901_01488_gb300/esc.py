@@ -87,6 +87,7 @@ _sig = {
     "esc_selectivity_batch_async": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32,
                                      ctypes.POINTER(esc_rows), _P, _P, _P], _S),
     "esc_debug_fail_allocs": ([ctypes.c_int32], _S),
+    "esc_debug_write_units": ([ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)], _S),
     "esc_build_checked": ([ctypes.POINTER(ctypes.c_int32)], _S),
     "esc_mlp_forward": ([_P, ctypes.c_uint64, _P, _P, _P, _P], _S),
     "esc_mlp_grad": ([_P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P], _S),
@@ -383,6 +384,15 @@ def esc_mlp_adam(params: torch.Tensor, w_bf16: torch.Tensor, grad: torch.Tensor,
 
 def esc_debug_fail_allocs(n: int) -> None:
     _check(_lib.esc_debug_fail_allocs(n), "esc_debug_fail_allocs")
+
+
+def esc_debug_write_units(nrows: int, slots: int) -> Tuple[int, int, int]:
+    """(groups per compaction unit, units, group-to-unit reciprocal) of a
+    materialising call on `nrows` rows with `slots` write-kernel blocks
+    resident (0: a batch's full-size units)."""
+    out = (ctypes.c_uint32 * 3)()
+    _check(_lib.esc_debug_write_units(nrows, slots, out), "esc_debug_write_units")
+    return out[0], out[1], out[2]
 
 
 def esc_build_checked() -> bool:

@@ -290,3 +290,40 @@ def test_checked_build_loads_and_says_so(esc):
     env = dict(os.environ, ESC_CHECKED="1")
     r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+
+
+def test_write_unit_layout(esc):
+    """Compaction units of a materialising call: 1..256 groups of 256 rows
+    each, covering every group; with `slots` write-kernel blocks resident,
+    as many whole waves as 256-group units need, with units as small as
+    fill them; a batch (slots 0) keeps 256-group units.  The group-to-unit
+    reciprocal divides every group index of the largest table exactly."""
+    rng = np.random.default_rng(5)
+    sizes = [0, 1, 255, 256, 257, 65536, 65537, 1_000_000, 8_000_000, 39_845_888, 39_845_889,
+             60_000_000, 600_000_000, esc.MAX_ROWS] + [int(x) for x in rng.integers(1, esc.MAX_ROWS, 30)]
+    for slots in (0, 1, 7, 608, 1216):
+        for n in sizes:
+            ug, nw, _ = esc.esc_debug_write_units(n, slots)
+            groups = (n + 255) // 256
+            assert 1 <= ug <= 256, (n, slots, ug)
+            assert nw == -(-groups // ug), (n, slots)
+            if slots == 0:
+                assert ug == 256
+            elif groups:
+                waves = -(-groups // (256 * slots))
+                assert -(-nw // slots) == waves, (n, slots, nw)
+                if ug > 1:   # one group fewer per unit would need another wave
+                    assert -(-groups // (ug - 1)) > waves * slots, (n, slots, ug)
+    top = (esc.MAX_ROWS + 255) // 256          # group indices run below this
+    for ug in range(1, 257):
+        got, nw, recip = esc.esc_debug_write_units(256 * ug, 1)
+        assert (got, nw) == (ug, 1)
+        gs = {0, 1, ug - 1, ug, ug + 1, top - 1, top - 2} | {k * ug + d for k in (top // ug - 1, top // ug)
+                                                              for d in (-1, 0, 1)}
+        gs |= {int(x) for x in rng.integers(0, top, 200)}
+        for g in sorted(x for x in gs if 0 <= x < top):
+            assert ((g * recip) >> 32 if recip else g) == g // ug, (ug, g)
+    with pytest.raises(esc.EscError):
+        esc.esc_debug_write_units(esc.MAX_ROWS + 1, 608)
+    with pytest.raises(esc.EscError):
+        esc.esc_debug_write_units(1000, -1)
